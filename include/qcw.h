@@ -1,0 +1,180 @@
+/*
+ * qcw: density-matrix simulator on one GB300 (sm_103a), C ABI.
+ *
+ * The state is an n-qubit density matrix rho, a 2^n x 2^n complex matrix kept on the
+ * device as row-major interleaved complex64 (float re, float im); element (r, c) sits at
+ * offset r * 2^n + c.  A basis label is r = sum_i q_i 2^(n-1-i): API qubit i is the
+ * paper's qubit i_s = i + 1 and qubit 0 is the most significant bit (Sec. 2.3,
+ * Eq. staten).  Its "stride" 2^(n-1-i) is the distance between partner labels n0 and n1
+ * (Sec. 3.1, Eqs. pair0 / pair1 and the text after Eq. resmat1).
+ *
+ * Operator matrices passed in are row-major interleaved complex128 (double re, double im)
+ * on the host.  A k-qubit matrix is indexed by the binary number q_{s1} q_{s2} ... q_{sk}
+ * of its qubits in the order the caller lists them; for k = 2 this is the amplitude-quartet
+ * order n00, n01, n10, n11 of Eq. resmat2 (V_{ij;kl} = <i j| V |k l>).  Matrices are copied
+ * during the call: the caller may free or reuse them as soon as the call returns.
+ *
+ * Arithmetic: gate and channel updates in FP32 complex; trace, purity, probabilities,
+ * partial traces and the post-measurement scale in FP64.
+ *
+ * Ordering: apply calls are asynchronous on the context's CUDA stream.  Every readout
+ * (trace, purity, probabilities, measure, partial trace, get_state) synchronises the
+ * stream and returns host FP64 values.
+ *
+ * Errors: every call returns a qcw_status.  Invalid arguments (NULL pointers, qubit out of
+ * range or repeated, k out of range, nkraus < 1, non-finite matrix entries) return
+ * QCW_EINVAL and leave the state unchanged.  A CUDA runtime failure returns QCW_ECUDA;
+ * qcw_last_error() then holds the runtime's message.
+ */
+#ifndef QCW_H
+#define QCW_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define QCW_API __attribute__((visibility("default")))
+#else
+#define QCW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qcw_ctx qcw_ctx;
+
+typedef enum {
+    QCW_OK = 0,
+    QCW_EINVAL = 1,     /* bad argument; state unchanged */
+    QCW_ENOMEM = 2,     /* device or host allocation failed */
+    QCW_ECUDA = 3,      /* CUDA runtime error (see qcw_last_error) */
+    QCW_EZEROPROB = 4,  /* measurement outcome with probability < 1e-12; state unchanged */
+    QCW_ETIMEOUT = 5,   /* a bounded wait ran out */
+    QCW_ENOTSUP = 6     /* size or mode not supported by this build */
+} qcw_status;
+
+/* Execution modes (qcw_set_mode). */
+#define QCW_MODE_PLAIN 0 /* each apply call launches its own kernel at once */
+#define QCW_MODE_FUSED 1 /* apply calls are queued; flush packs them into fused passes */
+
+/* Largest register size: rho of 17 qubits is 128 GiB of complex64. */
+#define QCW_MAX_QUBITS 17
+/* Largest k accepted by qcw_apply_gate. */
+#define QCW_MAX_GATE_QUBITS 5
+
+/* --------------------------------------------------------------------- lifetime */
+
+/* Create a context that owns a device rho of nqubits (1..QCW_MAX_QUBITS) and its own
+ * non-blocking CUDA stream on the current device; rho starts as |0..0><0..0|
+ * (the paper's initial state |0...0>, Sec. 4.1).  *out receives the handle. */
+QCW_API qcw_status qcw_create(int nqubits, qcw_ctx **out);
+
+/* Create a context on caller-owned memory: dev_rho points to 4^n complex64 values on the
+ * current device (16-byte aligned), cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  The context never frees dev_rho or the stream; its contents are used as is. */
+QCW_API qcw_status qcw_create_from_ptr(int nqubits, void *dev_rho, void *cuda_stream, qcw_ctx **out);
+
+/* Release the context (waits for its stream).  NULL is accepted. */
+QCW_API qcw_status qcw_destroy(qcw_ctx *ctx);
+
+/* Select QCW_MODE_PLAIN or QCW_MODE_FUSED.  fuse_k (2..QCW_MAX_GATE_QUBITS, 0 = let the
+ * tuner choose) bounds the number of qubits one fused pass may touch.  Switching mode
+ * flushes queued work first. */
+QCW_API qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k);
+
+/* Device pointer of rho and the context's stream (borrowed; valid until destroy). */
+QCW_API qcw_status qcw_get_device_state(qcw_ctx *ctx, void **dev_rho, void **cuda_stream);
+
+/* Number of qubits of the context. */
+QCW_API int qcw_nqubits(const qcw_ctx *ctx);
+
+/* ------------------------------------------------------------------------ state */
+
+/* rho <- |0..0><0..0|. */
+QCW_API qcw_status qcw_reset(qcw_ctx *ctx);
+
+/* rho <- host matrix: 2 * 4^n doubles, row-major interleaved complex128 (converted to
+ * complex64 on the device).  The buffer may be pageable or pinned. */
+QCW_API qcw_status qcw_set_state(qcw_ctx *ctx, const double *rho_c128);
+
+/* Same from host complex64 (2 * 4^n floats), copied without conversion. */
+QCW_API qcw_status qcw_set_state_c64(qcw_ctx *ctx, const float *rho_c64);
+
+/* Host copy of rho as complex128 (2 * 4^n doubles).  Synchronises. */
+QCW_API qcw_status qcw_get_state(qcw_ctx *ctx, double *rho_c128_out);
+
+/* ------------------------------------------------------------------- evolution */
+
+/* rho <- U rho U^dagger for a one-qubit U (2x2, 8 doubles) on `target`: the paper's
+ * pair update (Sec. 3.1, Eq. resmat1) on the row label with U and on the column label
+ * with conj(U).  With ncontrols > 0 the pair update happens only where every qubit in
+ * controls[] is 1 (a controlled-U); controls may be NULL when ncontrols == 0. */
+QCW_API qcw_status qcw_apply_gate1(qcw_ctx *ctx, const double u[8], int target, const int *controls,
+                           int ncontrols);
+
+/* rho <- V rho V^dagger for a two-qubit V (4x4, 32 doubles) on (q1, q2), index
+ * 2 * q(q1) + q(q2): the amplitude-quartet update of Sec. 3.2 (Eqs. twoopB, resmat2) on
+ * rows with V and on columns with conj(V).  Controls as for qcw_apply_gate1. */
+QCW_API qcw_status qcw_apply_gate2(qcw_ctx *ctx, const double u[32], int q1, int q2, const int *controls,
+                           int ncontrols);
+
+/* rho <- U rho U^dagger for a k-qubit U (1 <= k <= QCW_MAX_GATE_QUBITS; 2^k x 2^k, 2 * 4^k
+ * doubles) on qubits[0..k-1]: the octet update of Sec. 3.3 generalised to 2^k-member groups. */
+QCW_API qcw_status qcw_apply_gate(qcw_ctx *ctx, const double *u, const int *qubits, int k);
+
+/* rho <- sum_j K_j rho K_j^dagger (the Kraus / POVM form of the paper's ensemble average,
+ * Sec. 5.2.2, Eq. rhoE2) for nkraus (1..16) operators of k (1 or 2) qubits, stored one after
+ * another (nkraus * 2 * 4^k doubles).  Trace-decreasing sets are accepted as given. */
+QCW_API qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkraus, const int *qubits,
+                           int k);
+
+/* Launch queued fused work (no-op in plain mode). */
+QCW_API qcw_status qcw_flush(qcw_ctx *ctx);
+
+/* Flush and wait for the context's stream. */
+QCW_API qcw_status qcw_sync(qcw_ctx *ctx);
+
+/* ---------------------------------------------------------------------- readout */
+
+/* Tr rho = sum_i rho_ii (FP64).  Synchronises. */
+QCW_API qcw_status qcw_trace(qcw_ctx *ctx, double *re, double *im);
+
+/* sum_ij |rho_ij|^2, which equals Tr[rho . rho] (Sec. 5.2.3) for Hermitian rho (FP64). */
+QCW_API qcw_status qcw_purity(qcw_ctx *ctx, double *out);
+
+/* p1_out[i] = sum over labels r with qubit i equal to 1 of Re rho_rr, i = 0..n-1 (FP64). */
+QCW_API qcw_status qcw_probabilities(qcw_ctx *ctx, double *p1_out);
+
+/* Projective measurement of `qubit` (the ancilla read-out of Sec. 5.4.1; textbook form):
+ * p_m = sum_{r: q(r) = m} Re rho_rr; the outcome m is `forced` when it is 0 or 1,
+ * otherwise m = 0 iff u < p_0 (u: caller's uniform draw in [0, 1)).  Then
+ * rho <- P_m rho P_m / p_m with the scale computed in FP64.  *outcome and *prob receive m
+ * and p_m.  If p_m < 1e-12 the call returns QCW_EZEROPROB and rho is unchanged. */
+QCW_API qcw_status qcw_measure(qcw_ctx *ctx, int qubit, int forced, double u, int *outcome, double *prob);
+
+/* Reduced density matrix of the kept qubits (strictly ascending, 0 <= nkeep <= n):
+ * out[a, a'] = sum_b rho[(a b), (a' b)], where the first kept qubit is the most significant
+ * bit of a.  out_c128 receives 2 * 4^nkeep doubles (subsystem states of Sec. 5.2.3). */
+QCW_API qcw_status qcw_partial_trace(qcw_ctx *ctx, const int *keep, int nkeep, double *out_c128);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Message of the last failure on this thread ("" if none). */
+QCW_API const char *qcw_last_error(void);
+
+/* Static text for a status code. */
+QCW_API const char *qcw_strerror(qcw_status st);
+
+/* Counters since creation or the last qcw_stats_reset: kernel launches of this library,
+ * fused passes, and the summed device time (ms) of the fused-pass kernels when
+ * timing is enabled with qcw_enable_pass_timing(ctx, 1).  Any pointer may be NULL. */
+QCW_API qcw_status qcw_stats(qcw_ctx *ctx, long long *launches, long long *fused_passes,
+                     double *fused_pass_ms, long long *timed_passes);
+QCW_API qcw_status qcw_stats_reset(qcw_ctx *ctx);
+QCW_API qcw_status qcw_enable_pass_timing(qcw_ctx *ctx, int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCW_H */

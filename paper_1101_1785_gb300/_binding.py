@@ -1,0 +1,268 @@
+"""ctypes binding of libqcw.so: argument marshalling only.
+
+Every function of include/qcw.h is reachable under its C name through ``lib()``; the
+``Density`` class wraps one context and converts numpy arrays to the pointers and sizes
+the C ABI expects.  No computation happens here: each call goes to the CUDA library, and
+loading fails loudly when the library has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqcw.so")
+
+QCW_OK, QCW_EINVAL, QCW_ENOMEM, QCW_ECUDA, QCW_EZEROPROB, QCW_ETIMEOUT, QCW_ENOTSUP = range(7)
+QCW_MODE_PLAIN, QCW_MODE_FUSED = 0, 1
+QCW_MAX_QUBITS = 17
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+D = ctypes.c_double
+LL = ctypes.c_longlong
+PP = ctypes.POINTER(ctypes.c_void_p)
+PD = ctypes.POINTER(ctypes.c_double)
+PI = ctypes.POINTER(ctypes.c_int)
+PLL = ctypes.POINTER(ctypes.c_longlong)
+
+# name -> (restype, argtypes) for every declaration of include/qcw.h
+SIGNATURES = {
+    "qcw_create": (I, [I, PP]),
+    "qcw_create_from_ptr": (I, [I, P, P, PP]),
+    "qcw_destroy": (I, [P]),
+    "qcw_set_mode": (I, [P, I, I]),
+    "qcw_get_device_state": (I, [P, PP, PP]),
+    "qcw_nqubits": (I, [P]),
+    "qcw_reset": (I, [P]),
+    "qcw_set_state": (I, [P, P]),
+    "qcw_set_state_c64": (I, [P, P]),
+    "qcw_get_state": (I, [P, P]),
+    "qcw_apply_gate1": (I, [P, P, I, P, I]),
+    "qcw_apply_gate2": (I, [P, P, I, I, P, I]),
+    "qcw_apply_gate": (I, [P, P, P, I]),
+    "qcw_apply_kraus": (I, [P, P, I, P, I]),
+    "qcw_flush": (I, [P]),
+    "qcw_sync": (I, [P]),
+    "qcw_trace": (I, [P, PD, PD]),
+    "qcw_purity": (I, [P, PD]),
+    "qcw_probabilities": (I, [P, P]),
+    "qcw_measure": (I, [P, I, I, D, PI, PD]),
+    "qcw_partial_trace": (I, [P, P, I, P]),
+    "qcw_last_error": (ctypes.c_char_p, []),
+    "qcw_strerror": (ctypes.c_char_p, [I]),
+    "qcw_stats": (I, [P, PLL, PLL, PD, PLL]),
+    "qcw_stats_reset": (I, [P]),
+    "qcw_enable_pass_timing": (I, [P, I]),
+}
+
+
+class QcwError(RuntimeError):
+    def __init__(self, status: int, what: str, msg: str):
+        super().__init__(f"{what}: status {status} ({msg})")
+        self.status = status
+
+
+def lib(path: str | None = None):
+    """Load libqcw.so once (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"qcw CUDA library missing at {p}: run __graft_entry__.build()")
+            L = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str):
+    if status != QCW_OK:
+        L = lib()
+        raise QcwError(status, what, L.qcw_last_error().decode() or L.qcw_strerror(status).decode())
+
+
+def _mat(u, dim: int) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(u, dtype=np.complex128))
+    if a.size != dim:
+        raise ValueError(f"expected {dim} complex entries, got {a.size}")
+    return a
+
+
+def _ints(xs) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(list(xs), dtype=np.int32))
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(P) if a is not None and a.size else None
+
+
+class Density:
+    """One qcw context: a device density matrix of n qubits and its stream."""
+
+    def __init__(self, n: int, dev_ptr: int | None = None, stream: int | None = None):
+        L = lib()
+        h = P()
+        if dev_ptr is None:
+            check(L.qcw_create(int(n), ctypes.byref(h)), "qcw_create")
+        else:
+            check(L.qcw_create_from_ptr(int(n), P(dev_ptr), P(stream or 0), ctypes.byref(h)), "qcw_create_from_ptr")
+        self.h = h
+        self.n = int(n)
+
+    @classmethod
+    def from_tensor(cls, t, stream=None) -> "Density":
+        """Borrow a torch tensor of 4^n complex64 values (and a torch.cuda.Stream)."""
+        n = (int(t.numel()).bit_length() - 1) // 2
+        sp = 0 if stream is None else int(stream.cuda_stream)
+        return cls(n, t.data_ptr(), sp)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().qcw_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- configuration / state
+    def set_mode(self, mode: int, fuse_k: int = 0):
+        check(lib().qcw_set_mode(self.h, int(mode), int(fuse_k)), "qcw_set_mode")
+
+    def device_state(self):
+        r, s = P(), P()
+        check(lib().qcw_get_device_state(self.h, ctypes.byref(r), ctypes.byref(s)), "qcw_get_device_state")
+        return r.value, s.value
+
+    def reset(self):
+        check(lib().qcw_reset(self.h), "qcw_reset")
+
+    def set_state(self, rho: np.ndarray):
+        a = np.ascontiguousarray(rho, dtype=np.complex128)
+        assert a.shape == (1 << self.n, 1 << self.n)
+        check(lib().qcw_set_state(self.h, _p(a)), "qcw_set_state")
+
+    def set_state_c64(self, host_ptr: int):
+        """Upload from a host buffer of 4^n complex64 (e.g. a pinned torch tensor's data_ptr)."""
+        check(lib().qcw_set_state_c64(self.h, P(host_ptr)), "qcw_set_state_c64")
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty((1 << self.n, 1 << self.n), dtype=np.complex128)
+        check(lib().qcw_get_state(self.h, _p(out)), "qcw_get_state")
+        return out
+
+    # ---------------------------------------------------------------- evolution
+    def apply_gate1(self, u, target: int, controls=()):
+        m = _mat(u, 4)
+        c = _ints(controls)
+        check(lib().qcw_apply_gate1(self.h, _p(m), int(target), _p(c), len(c)), "qcw_apply_gate1")
+
+    def apply_gate2(self, u, q1: int, q2: int, controls=()):
+        m = _mat(u, 16)
+        c = _ints(controls)
+        check(lib().qcw_apply_gate2(self.h, _p(m), int(q1), int(q2), _p(c), len(c)), "qcw_apply_gate2")
+
+    def apply_gate(self, u, qubits):
+        q = _ints(qubits)
+        m = _mat(u, 1 << (2 * len(q)))
+        check(lib().qcw_apply_gate(self.h, _p(m), _p(q), len(q)), "qcw_apply_gate")
+
+    def apply_kraus(self, kraus, qubits):
+        q = _ints(qubits)
+        ks = np.ascontiguousarray(np.asarray(kraus, dtype=np.complex128))
+        nk = ks.shape[0] if ks.ndim == 3 else 1
+        if ks.size != nk << (2 * len(q)):
+            raise ValueError("Kraus array has the wrong size")
+        check(lib().qcw_apply_kraus(self.h, _p(ks), nk, _p(q), len(q)), "qcw_apply_kraus")
+
+    def apply_op(self, op):
+        """Apply one workloads.Op (gate or Kraus channel)."""
+        if op.kind == "gate":
+            if op.k == 1:
+                self.apply_gate1(op.mats[0], op.qubits[0])
+            elif op.k == 2:
+                self.apply_gate2(op.mats[0], op.qubits[0], op.qubits[1])
+            else:
+                self.apply_gate(op.mats[0], op.qubits)
+        else:
+            self.apply_kraus(op.mats, op.qubits)
+
+    def flush(self):
+        check(lib().qcw_flush(self.h), "qcw_flush")
+
+    def sync(self):
+        check(lib().qcw_sync(self.h), "qcw_sync")
+
+    # ---------------------------------------------------------------- readouts
+    def trace(self) -> complex:
+        re, im = D(), D()
+        check(lib().qcw_trace(self.h, ctypes.byref(re), ctypes.byref(im)), "qcw_trace")
+        return complex(re.value, im.value)
+
+    def purity(self) -> float:
+        v = D()
+        check(lib().qcw_purity(self.h, ctypes.byref(v)), "qcw_purity")
+        return v.value
+
+    def probabilities(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.float64)
+        check(lib().qcw_probabilities(self.h, _p(out)), "qcw_probabilities")
+        return out
+
+    def measure(self, qubit: int, forced: int = -1, u: float = 0.0):
+        oc, pr = I(), D()
+        check(lib().qcw_measure(self.h, int(qubit), int(forced), float(u), ctypes.byref(oc), ctypes.byref(pr)),
+              "qcw_measure")
+        return oc.value, pr.value
+
+    def partial_trace(self, keep) -> np.ndarray:
+        k = _ints(sorted(keep))
+        out = np.zeros((1 << len(k), 1 << len(k)), dtype=np.complex128)
+        check(lib().qcw_partial_trace(self.h, _p(k), len(k), _p(out)), "qcw_partial_trace")
+        return out
+
+    # ---------------------------------------------------------------- diagnostics
+    def enable_pass_timing(self, on: bool = True):
+        check(lib().qcw_enable_pass_timing(self.h, int(bool(on))), "qcw_enable_pass_timing")
+
+    def stats(self) -> dict:
+        la, ps, ts = LL(), LL(), LL()
+        ms = D()
+        check(lib().qcw_stats(self.h, ctypes.byref(la), ctypes.byref(ps), ctypes.byref(ms), ctypes.byref(ts)),
+              "qcw_stats")
+        return {"launches": la.value, "fused_passes": ps.value, "fused_pass_ms": ms.value, "timed_passes": ts.value}
+
+    def stats_reset(self):
+        check(lib().qcw_stats_reset(self.h), "qcw_stats_reset")
+
+
+def run_circuit(circuit, dens: Density | None = None, ops=None) -> Density:
+    """Apply a workloads.Circuit through the C ABI (initial state uploaded when given)."""
+    d = dens or Density(circuit.n)
+    if circuit.init == "matrix":
+        d.set_state(circuit.rho0)
+    else:
+        d.reset()
+    for op in (circuit.ops if ops is None else ops):
+        d.apply_op(op)
+    return d

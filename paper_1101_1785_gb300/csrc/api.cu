@@ -1,0 +1,631 @@
+// C ABI of the qcw library: argument checks, context lifetime, the plain (one launch per
+// operation) path and the FP64 readouts.  The fused path lives in fused.cu / planner.cpp.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "qcw_internal.h"
+
+using namespace qcw;
+
+static thread_local std::string g_err;
+
+qcw_status qcw::set_error(qcw_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+qcw_status qcw::cuda_error(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return QCW_ECUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_error(e_, #call);       \
+    } while (0)
+
+#define CKLAUNCH(ctx, nlaunch)                                     \
+    do {                                                           \
+        (ctx)->launches += (nlaunch);                              \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return cuda_error(e_, "kernel launch"); \
+    } while (0)
+
+#define CHECK_CTX(ctx)                                                             \
+    do {                                                                           \
+        if (!(ctx)) return set_error(QCW_EINVAL, "null context");                  \
+    } while (0)
+
+// ------------------------------------------------------------------ argument checks
+static bool all_finite(const double *a, size_t cnt)
+{
+    for (size_t i = 0; i < cnt; i++)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+static qcw_status check_qubits(int n, const int *qs, int k, const int *ctrl, int nc)
+{
+    if (k < 1 || nc < 0 || k + nc > n) return set_error(QCW_EINVAL, "bad qubit count");
+    if (!qs || (nc > 0 && !ctrl)) return set_error(QCW_EINVAL, "null qubit list");
+    unsigned seen = 0;
+    for (int j = 0; j < k + nc; j++) {
+        int q = j < k ? qs[j] : ctrl[j - k];
+        if (q < 0 || q >= n) return set_error(QCW_EINVAL, "qubit index out of range");
+        if (seen & (1u << q)) return set_error(QCW_EINVAL, "repeated qubit");
+        seen |= 1u << q;
+    }
+    return QCW_OK;
+}
+
+static std::vector<c128> to_c128(const double *a, size_t count)
+{
+    std::vector<c128> v(count);
+    for (size_t i = 0; i < count; i++) v[i] = c128(a[2 * i], a[2 * i + 1]);
+    return v;
+}
+
+static float2 f2(c128 z) { return make_float2((float)z.real(), (float)z.imag()); }
+
+// Superoperator of a Kraus set on k qubits: S[(r',c'), (r,c)] = sum_j K_j[r', r] conj(K_j[c', c]),
+// so that rho'_{r'c'} = sum_{rc} S rho_{rc} = sum_j (K_j rho K_j^dagger)_{r'c'} (Eq. rhoE2).
+static std::vector<c128> kraus_superop(const std::vector<c128> &ks, int nk, int k)
+{
+    int d = 1 << k, D = d * d;
+    std::vector<c128> s((size_t)D * D, c128(0, 0));
+    for (int j = 0; j < nk; j++) {
+        const c128 *K = ks.data() + (size_t)j * d * d;
+        for (int r2 = 0; r2 < d; r2++)
+            for (int c2 = 0; c2 < d; c2++)
+                for (int r = 0; r < d; r++)
+                    for (int c = 0; c < d; c++)
+                        s[(size_t)(r2 * d + c2) * D + (r * d + c)] += K[r2 * d + r] * std::conj(K[c2 * d + c]);
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ plain launches
+namespace qcw {
+
+qcw_status plain_gate1(qcw_ctx *c, const c128 *u, int t, const int *ctrl, int nc)
+{
+    const int n = c->n;
+    Gate1Params p{};
+    for (int i = 0; i < 4; i++) p.u[i] = f2(u[i]);
+    p.pc = n - 1 - t;
+    p.pr = 2 * n - 1 - t;
+    for (int j = 0; j < nc; j++) {
+        p.cmask_c |= 1ull << (n - 1 - ctrl[j]);
+        p.cmask_r |= 1ull << (2 * n - 1 - ctrl[j]);
+    }
+    launch_gate1(p, c->rho, n, c->nsm, c->stream);
+    CKLAUNCH(c, 1);
+    return QCW_OK;
+}
+
+static void quartet_layout(int n, int q1, int q2, int *pos, uint64_t *offr, uint64_t *offc)
+{
+    int pr1 = 2 * n - 1 - q1, pr2 = 2 * n - 1 - q2, pc1 = n - 1 - q1, pc2 = n - 1 - q2;
+    int v[4] = {pc1, pc2, pr1, pr2};
+    for (int a = 0; a < 4; a++)
+        for (int b = a + 1; b < 4; b++)
+            if (v[b] < v[a]) { int t = v[a]; v[a] = v[b]; v[b] = t; }
+    for (int a = 0; a < 4; a++) pos[a] = v[a];
+    for (int i = 0; i < 4; i++) {
+        offr[i] = (((uint64_t)(i >> 1) & 1) << pr1) | (((uint64_t)i & 1) << pr2);
+        offc[i] = (((uint64_t)(i >> 1) & 1) << pc1) | (((uint64_t)i & 1) << pc2);
+    }
+}
+
+qcw_status plain_gate2(qcw_ctx *c, const c128 *u, int q1, int q2, const int *ctrl, int nc)
+{
+    const int n = c->n;
+    Gate2Params p{};
+    for (int i = 0; i < 16; i++) p.u[i] = f2(u[i]);
+    quartet_layout(n, q1, q2, p.pos, p.off_r, p.off_c);
+    for (int j = 0; j < nc; j++) {
+        p.cmask_c |= 1ull << (n - 1 - ctrl[j]);
+        p.cmask_r |= 1ull << (2 * n - 1 - ctrl[j]);
+    }
+    launch_gate2(p, c->rho, n, c->nsm, c->stream);
+    CKLAUNCH(c, 1);
+    return QCW_OK;
+}
+
+// k-qubit dense gate as two passes: U on the row labels, then conj(U) on the column labels.
+qcw_status plain_gatek(qcw_ctx *c, const c128 *u, const int *qs, int k)
+{
+    const int n = c->n, m = 1 << k;
+    for (int side = 0; side < 2; side++) {
+        GateKParams p{};
+        p.k = k;
+        int base = side == 0 ? 2 * n - 1 : n - 1;  // row bits, then column bits
+        for (int i = 0; i < m * m; i++) p.u[i] = f2(side == 0 ? u[i] : std::conj(u[i]));
+        int v[5];
+        for (int j = 0; j < k; j++) v[j] = base - qs[j];
+        for (int i = 0; i < m; i++) {
+            uint64_t o = 0;
+            for (int j = 0; j < k; j++)
+                if ((i >> (k - 1 - j)) & 1) o |= 1ull << v[j];
+            p.off[i] = o;
+        }
+        for (int a = 0; a < k; a++)
+            for (int b = a + 1; b < k; b++)
+                if (v[b] < v[a]) { int t = v[a]; v[a] = v[b]; v[b] = t; }
+        for (int j = 0; j < k; j++) p.pos[j] = v[j];
+        launch_gatek_side(p, c->rho, n, c->nsm, c->stream);
+        CKLAUNCH(c, 1);
+    }
+    return QCW_OK;
+}
+
+qcw_status plain_super(qcw_ctx *c, const std::vector<c128> &s, const int *qs, int k)
+{
+    const int n = c->n;
+    if (k == 1) {
+        Super1Params p{};
+        for (int i = 0; i < 16; i++) p.s[i] = f2(s[i]);
+        p.pc = n - 1 - qs[0];
+        p.pr = 2 * n - 1 - qs[0];
+        launch_super1(p, c->rho, n, c->nsm, c->stream);
+    } else if (k == 2) {
+        Super2Params p{};
+        for (int i = 0; i < 256; i++) p.s[i] = f2(s[i]);
+        quartet_layout(n, qs[0], qs[1], p.pos, p.off_r, p.off_c);
+        launch_super2(p, c->rho, n, c->nsm, c->stream);
+    } else {
+        return set_error(QCW_ENOTSUP, "channels act on 1 or 2 qubits");
+    }
+    CKLAUNCH(c, 1);
+    return QCW_OK;
+}
+
+qcw_status plain_apply(qcw_ctx *c, const QOp &op)
+{
+    if (op.kind == 1) return plain_super(c, op.m, op.qubits, op.k);
+    if (op.k == 1) return plain_gate1(c, op.m.data(), op.qubits[0], op.controls, op.ncontrols);
+    if (op.k == 2) return plain_gate2(c, op.m.data(), op.qubits[0], op.qubits[1], op.controls, op.ncontrols);
+    return plain_gatek(c, op.m.data(), op.qubits, op.k);
+}
+
+}  // namespace qcw
+
+static qcw_status submit(qcw_ctx *c, QOp &&op)
+{
+    if (c->mode == QCW_MODE_FUSED && op.ncontrols == 0) {
+        c->queue.push_back(std::move(op));
+        return QCW_OK;
+    }
+    if (c->mode == QCW_MODE_FUSED) {
+        qcw_status st = fused_flush(c);
+        if (st) return st;
+    }
+    return plain_apply(c, op);
+}
+
+// ------------------------------------------------------------------ lifetime
+static void ctx_free(qcw_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    fused_destroy(c);
+    if (c->owns_rho && c->rho) cudaFree(c->rho);
+    if (c->d_partials) cudaFree(c->d_partials);
+    if (c->d_result) cudaFree(c->d_result);
+    if (c->h_result) cudaFreeHost(c->h_result);
+    if (c->d_staging) cudaFree(c->d_staging);
+    if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+static qcw_status ctx_common(qcw_ctx *c)
+{
+    CK(cudaGetDevice(&c->dev));
+    CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
+    c->red_blocks = reduce_blocks(c->nsm);
+    if (cudaMalloc(&c->d_partials, sizeof(double) * (size_t)c->red_blocks * (QCW_MAX_QUBITS + 2)) != cudaSuccess)
+        return set_error(QCW_ENOMEM, "reduction scratch");
+    if (cudaMalloc(&c->d_result, 64 * sizeof(double)) != cudaSuccess) return set_error(QCW_ENOMEM, "result block");
+    if (cudaMallocHost(&c->h_result, 64 * sizeof(double)) != cudaSuccess) return set_error(QCW_ENOMEM, "pinned result");
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_create(int nqubits, qcw_ctx **out)
+{
+    if (!out) return set_error(QCW_EINVAL, "null out");
+    *out = nullptr;
+    if (nqubits < 1 || nqubits > QCW_MAX_QUBITS) return set_error(QCW_EINVAL, "nqubits out of range");
+    qcw_ctx *c = new qcw_ctx();
+    c->n = nqubits;
+    qcw_status st = ctx_common(c);
+    if (!st) {
+        size_t bytes = sizeof(float2) << (2 * nqubits);
+        if (cudaMalloc(&c->rho, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            st = set_error(QCW_ENOMEM, "rho allocation");
+        } else {
+            c->owns_rho = true;
+        }
+    }
+    if (!st) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) st = cuda_error(e, "stream");
+        else c->owns_stream = true;
+    }
+    if (!st) st = qcw_reset(c);
+    if (st) {
+        ctx_free(c);
+        return st;
+    }
+    *out = c;
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_create_from_ptr(int nqubits, void *dev_rho, void *cuda_stream, qcw_ctx **out)
+{
+    if (!out) return set_error(QCW_EINVAL, "null out");
+    *out = nullptr;
+    if (nqubits < 1 || nqubits > QCW_MAX_QUBITS) return set_error(QCW_EINVAL, "nqubits out of range");
+    if (!dev_rho || (reinterpret_cast<uintptr_t>(dev_rho) & 15)) return set_error(QCW_EINVAL, "rho must be 16-byte aligned");
+    qcw_ctx *c = new qcw_ctx();
+    c->n = nqubits;
+    c->rho = static_cast<float2 *>(dev_rho);
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    qcw_status st = ctx_common(c);
+    if (st) {
+        ctx_free(c);
+        return st;
+    }
+    *out = c;
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_destroy(qcw_ctx *ctx)
+{
+    ctx_free(ctx);
+    return QCW_OK;
+}
+
+extern "C" int qcw_nqubits(const qcw_ctx *ctx) { return ctx ? ctx->n : -1; }
+
+extern "C" qcw_status qcw_get_device_state(qcw_ctx *ctx, void **dev_rho, void **cuda_stream)
+{
+    CHECK_CTX(ctx);
+    if (dev_rho) *dev_rho = ctx->rho;
+    if (cuda_stream) *cuda_stream = ctx->stream;
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k)
+{
+    CHECK_CTX(ctx);
+    if (mode != QCW_MODE_PLAIN && mode != QCW_MODE_FUSED) return set_error(QCW_EINVAL, "bad mode");
+    if (fuse_k != 0 && (fuse_k < 2 || fuse_k > QCW_MAX_GATE_QUBITS)) return set_error(QCW_EINVAL, "bad fuse_k");
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    ctx->mode = mode;
+    ctx->fuse_k = fuse_k;
+    return QCW_OK;
+}
+
+// ------------------------------------------------------------------ state
+extern "C" qcw_status qcw_reset(qcw_ctx *ctx)
+{
+    CHECK_CTX(ctx);
+    ctx->queue.clear();
+    launch_zero_state(ctx->rho, ctx->n, ctx->nsm, ctx->stream);
+    CKLAUNCH(ctx, 1);
+    return QCW_OK;
+}
+
+static const size_t kStageElems = (size_t)1 << 22;  // 4 Mi complex128 = 64 MiB per chunk
+
+static qcw_status ensure_staging(qcw_ctx *c)
+{
+    if (c->d_staging) return QCW_OK;
+    size_t bytes = kStageElems * sizeof(double2);
+    if (cudaMalloc(&c->d_staging, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(QCW_ENOMEM, "staging buffer");
+    }
+    c->staging_bytes = bytes;
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_set_state(qcw_ctx *ctx, const double *rho_c128)
+{
+    CHECK_CTX(ctx);
+    if (!rho_c128) return set_error(QCW_EINVAL, "null state");
+    qcw_status st = ensure_staging(ctx);
+    if (st) return st;
+    ctx->queue.clear();
+    size_t total = (size_t)1 << (2 * ctx->n);
+    for (size_t off = 0; off < total; off += kStageElems) {
+        size_t cnt = total - off < kStageElems ? total - off : kStageElems;
+        CK(cudaMemcpyAsync(ctx->d_staging, rho_c128 + 2 * off, cnt * sizeof(double2), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        launch_c128_to_c64(static_cast<const double2 *>(ctx->d_staging), ctx->rho + off, cnt, ctx->nsm, ctx->stream);
+        CKLAUNCH(ctx, 1);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_set_state_c64(qcw_ctx *ctx, const float *rho_c64)
+{
+    CHECK_CTX(ctx);
+    if (!rho_c64) return set_error(QCW_EINVAL, "null state");
+    ctx->queue.clear();
+    size_t bytes = sizeof(float2) << (2 * ctx->n);
+    CK(cudaMemcpyAsync(ctx->rho, rho_c64, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_get_state(qcw_ctx *ctx, double *out)
+{
+    CHECK_CTX(ctx);
+    if (!out) return set_error(QCW_EINVAL, "null output");
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    st = ensure_staging(ctx);
+    if (st) return st;
+    size_t total = (size_t)1 << (2 * ctx->n);
+    for (size_t off = 0; off < total; off += kStageElems) {
+        size_t cnt = total - off < kStageElems ? total - off : kStageElems;
+        launch_c64_to_c128(ctx->rho + off, static_cast<double2 *>(ctx->d_staging), cnt, ctx->nsm, ctx->stream);
+        CKLAUNCH(ctx, 1);
+        CK(cudaMemcpyAsync(out + 2 * off, ctx->d_staging, cnt * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return QCW_OK;
+}
+
+// ------------------------------------------------------------------ evolution
+extern "C" qcw_status qcw_apply_gate1(qcw_ctx *ctx, const double u[8], int target, const int *controls,
+                                      int ncontrols)
+{
+    CHECK_CTX(ctx);
+    if (!u) return set_error(QCW_EINVAL, "null matrix");
+    qcw_status st = check_qubits(ctx->n, &target, 1, controls, ncontrols);
+    if (st) return st;
+    if (!all_finite(u, 8)) return set_error(QCW_EINVAL, "non-finite matrix entry");
+    QOp op;
+    op.kind = 0;
+    op.k = 1;
+    op.qubits[0] = target;
+    op.ncontrols = ncontrols;
+    for (int j = 0; j < ncontrols; j++) op.controls[j] = controls[j];
+    op.m = to_c128(u, 4);
+    return submit(ctx, std::move(op));
+}
+
+extern "C" qcw_status qcw_apply_gate2(qcw_ctx *ctx, const double u[32], int q1, int q2, const int *controls,
+                                      int ncontrols)
+{
+    CHECK_CTX(ctx);
+    if (!u) return set_error(QCW_EINVAL, "null matrix");
+    int qs[2] = {q1, q2};
+    qcw_status st = check_qubits(ctx->n, qs, 2, controls, ncontrols);
+    if (st) return st;
+    if (!all_finite(u, 32)) return set_error(QCW_EINVAL, "non-finite matrix entry");
+    QOp op;
+    op.kind = 0;
+    op.k = 2;
+    op.qubits[0] = q1;
+    op.qubits[1] = q2;
+    op.ncontrols = ncontrols;
+    for (int j = 0; j < ncontrols; j++) op.controls[j] = controls[j];
+    op.m = to_c128(u, 16);
+    return submit(ctx, std::move(op));
+}
+
+extern "C" qcw_status qcw_apply_gate(qcw_ctx *ctx, const double *u, const int *qubits, int k)
+{
+    CHECK_CTX(ctx);
+    if (!u) return set_error(QCW_EINVAL, "null matrix");
+    if (k < 1 || k > QCW_MAX_GATE_QUBITS) return set_error(QCW_EINVAL, "k out of range");
+    qcw_status st = check_qubits(ctx->n, qubits, k, nullptr, 0);
+    if (st) return st;
+    size_t cnt = (size_t)1 << (2 * k);
+    if (!all_finite(u, 2 * cnt)) return set_error(QCW_EINVAL, "non-finite matrix entry");
+    QOp op;
+    op.kind = 0;
+    op.k = k;
+    for (int j = 0; j < k; j++) op.qubits[j] = qubits[j];
+    op.ncontrols = 0;
+    op.m = to_c128(u, cnt);
+    return submit(ctx, std::move(op));
+}
+
+extern "C" qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkraus, const int *qubits, int k)
+{
+    CHECK_CTX(ctx);
+    if (!kraus) return set_error(QCW_EINVAL, "null Kraus set");
+    if (k < 1 || k > 2) return set_error(QCW_EINVAL, "channels act on 1 or 2 qubits");
+    if (nkraus < 1 || nkraus > 16) return set_error(QCW_EINVAL, "nkraus out of range");
+    qcw_status st = check_qubits(ctx->n, qubits, k, nullptr, 0);
+    if (st) return st;
+    size_t cnt = (size_t)nkraus << (2 * k);
+    if (!all_finite(kraus, 2 * cnt)) return set_error(QCW_EINVAL, "non-finite matrix entry");
+    QOp op;
+    op.kind = 1;
+    op.k = k;
+    for (int j = 0; j < k; j++) op.qubits[j] = qubits[j];
+    op.ncontrols = 0;
+    op.m = kraus_superop(to_c128(kraus, cnt), nkraus, k);
+    return submit(ctx, std::move(op));
+}
+
+extern "C" qcw_status qcw_flush(qcw_ctx *ctx)
+{
+    CHECK_CTX(ctx);
+    return fused_flush(ctx);
+}
+
+extern "C" qcw_status qcw_sync(qcw_ctx *ctx)
+{
+    CHECK_CTX(ctx);
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return QCW_OK;
+}
+
+// ------------------------------------------------------------------ readouts
+static qcw_status diag_readout(qcw_ctx *c)
+{
+    qcw_status st = fused_flush(c);
+    if (st) return st;
+    launch_diag_reduce(c->rho, c->n, c->d_partials, c->d_result, c->red_blocks, c->stream);
+    CKLAUNCH(c, launches_per_reduce());
+    CK(cudaMemcpyAsync(c->h_result, c->d_result, sizeof(double) * (c->n + 2), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_trace(qcw_ctx *ctx, double *re, double *im)
+{
+    CHECK_CTX(ctx);
+    qcw_status st = diag_readout(ctx);
+    if (st) return st;
+    if (re) *re = ctx->h_result[0];
+    if (im) *im = ctx->h_result[1];
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_probabilities(qcw_ctx *ctx, double *p1_out)
+{
+    CHECK_CTX(ctx);
+    if (!p1_out) return set_error(QCW_EINVAL, "null output");
+    qcw_status st = diag_readout(ctx);
+    if (st) return st;
+    for (int q = 0; q < ctx->n; q++) p1_out[q] = ctx->h_result[2 + q];
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_purity(qcw_ctx *ctx, double *out)
+{
+    CHECK_CTX(ctx);
+    if (!out) return set_error(QCW_EINVAL, "null output");
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    launch_purity(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
+    CKLAUNCH(ctx, launches_per_reduce());
+    CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *out = ctx->h_result[0];
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_measure(qcw_ctx *ctx, int qubit, int forced, double u, int *outcome, double *prob)
+{
+    CHECK_CTX(ctx);
+    if (qubit < 0 || qubit >= ctx->n || forced < -1 || forced > 1) return set_error(QCW_EINVAL, "bad measurement");
+    if (!std::isfinite(u)) return set_error(QCW_EINVAL, "non-finite draw");
+    qcw_status st = diag_readout(ctx);
+    if (st) return st;
+    double p1 = ctx->h_result[2 + qubit];
+    double p0 = ctx->h_result[0] - p1;
+    int m = forced >= 0 ? forced : (u < p0 ? 0 : 1);
+    double pm = m ? p1 : p0;
+    if (outcome) *outcome = m;
+    if (prob) *prob = pm;
+    if (!(pm >= 1e-12)) return set_error(QCW_EZEROPROB, "outcome probability below 1e-12");
+    launch_project(ctx->rho, ctx->n, qubit, m, (float)(1.0 / pm), ctx->nsm, ctx->stream);
+    CKLAUNCH(ctx, 1);
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_partial_trace(qcw_ctx *ctx, const int *keep, int nkeep, double *out_c128)
+{
+    CHECK_CTX(ctx);
+    const int n = ctx->n;
+    if (!out_c128 || nkeep < 0 || nkeep > n || (nkeep > 0 && !keep)) return set_error(QCW_EINVAL, "bad partial trace");
+    for (int j = 0; j < nkeep; j++) {
+        if (keep[j] < 0 || keep[j] >= n) return set_error(QCW_EINVAL, "qubit index out of range");
+        if (j && keep[j] <= keep[j - 1]) return set_error(QCW_EINVAL, "kept qubits must ascend");
+    }
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    PTParams p{};
+    p.n = n;
+    p.nkeep = nkeep;
+    unsigned kept = 0;
+    for (int j = 0; j < nkeep; j++) {
+        p.kpos[j] = (int8_t)(n - 1 - keep[j]);
+        kept |= 1u << keep[j];
+    }
+    for (int q = 0; q < n; q++)
+        if (!(kept & (1u << q))) p.tpos[p.ntr++] = (int8_t)(n - 1 - q);
+    size_t nout = (size_t)1 << (2 * nkeep);
+    double2 *d_out = nullptr;
+    if (nout * sizeof(double2) <= 64 * sizeof(double)) {
+        d_out = reinterpret_cast<double2 *>(ctx->d_result);
+    } else {
+        if (cudaMallocAsync(&d_out, nout * sizeof(double2), ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QCW_ENOMEM, "partial trace output");
+        }
+    }
+    launch_partial_trace(ctx->rho, p, d_out, ctx->nsm, ctx->stream);
+    ctx->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_c128, d_out, nout * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream);
+    if (d_out != reinterpret_cast<double2 *>(ctx->d_result)) cudaFreeAsync(d_out, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(e, "partial trace");
+    return QCW_OK;
+}
+
+// ------------------------------------------------------------------ diagnostics
+extern "C" const char *qcw_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *qcw_strerror(qcw_status st)
+{
+    switch (st) {
+    case QCW_OK: return "ok";
+    case QCW_EINVAL: return "invalid argument";
+    case QCW_ENOMEM: return "out of memory";
+    case QCW_ECUDA: return "CUDA error";
+    case QCW_EZEROPROB: return "zero-probability outcome";
+    case QCW_ETIMEOUT: return "timeout";
+    case QCW_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+extern "C" qcw_status qcw_stats(qcw_ctx *ctx, long long *launches, long long *fused_passes, double *fused_pass_ms,
+                                long long *timed_passes)
+{
+    CHECK_CTX(ctx);
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    CK(cudaStreamSynchronize(ctx->stream));
+    fused_collect_timing(ctx);
+    if (launches) *launches = ctx->launches;
+    if (fused_passes) *fused_passes = ctx->passes;
+    if (fused_pass_ms) *fused_pass_ms = ctx->pass_ms;
+    if (timed_passes) *timed_passes = ctx->timed_passes;
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_stats_reset(qcw_ctx *ctx)
+{
+    CHECK_CTX(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));
+    fused_collect_timing(ctx);
+    ctx->launches = ctx->passes = ctx->timed_passes = 0;
+    ctx->pass_ms = 0;
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_enable_pass_timing(qcw_ctx *ctx, int on)
+{
+    CHECK_CTX(ctx);
+    ctx->timing = on != 0;
+    return QCW_OK;
+}

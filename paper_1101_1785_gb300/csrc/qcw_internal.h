@@ -1,0 +1,132 @@
+// Internal declarations of the qcw library (host side): the context, kernel parameter
+// blocks and the launchers implemented in the .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "qcw.h"
+
+namespace qcw {
+
+using c128 = std::complex<double>;
+
+// ------------------------------------------------------------------ kernel parameter blocks
+// Matrices travel by value in the kernel parameter space (constant bank): every thread
+// reads the same coefficient at the same time, which the constant cache broadcasts.
+
+struct Gate1Params {
+    float2 u[4];       // U row-major
+    int pc, pr;        // virtual bit positions of the target's column / row bit
+    uint64_t cmask_c;  // control qubits' column bits (all must be 1 for U^* on columns)
+    uint64_t cmask_r;  // control qubits' row bits (all must be 1 for U on rows)
+};
+
+struct Gate2Params {
+    float2 u[16];      // V row-major, index 2*q(q1) + q(q2)
+    int pos[4];        // the four virtual bit positions, ascending (for insertion)
+    uint64_t off_r[4]; // row offset of local row index i
+    uint64_t off_c[4]; // column offset of local column index j
+    uint64_t cmask_c, cmask_r;
+};
+
+struct Super1Params {
+    float2 s[16];      // 4x4 superoperator, local index e = 2*row_bit + col_bit
+    int pc, pr;
+};
+
+struct Super2Params {
+    float2 s[256];     // 16x16 superoperator, local index e = 4*row_local + col_local
+    int pos[4];
+    uint64_t off_r[4], off_c[4];
+};
+
+struct GateKParams {   // one side (rows or columns) of a k-qubit dense gate, k <= 5
+    float2 u[1024];    // U (or conj(U) for the column side), 2^k x 2^k row-major
+    int k;
+    int pos[5];        // ascending virtual bit positions of the struck bits on this side
+    uint64_t off[32];  // offset of local index i on this side
+};
+
+struct PTParams {
+    int n, nkeep, ntr;
+    int8_t kpos[QCW_MAX_QUBITS];  // label bit of kept qubit j; j = 0 is the result's MSB
+    int8_t tpos[QCW_MAX_QUBITS];  // label bit of traced qubit j
+};
+
+// ------------------------------------------------------------------ launchers (kernels.cu)
+void launch_gate1(const Gate1Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_gate2(const Gate2Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_super1(const Super1Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_super2(const Super2Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_gatek_side(const GateKParams &p, float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_zero_state(float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_c128_to_c64(const double2 *src, float2 *dst, size_t count, int nsm, cudaStream_t s);
+void launch_c64_to_c128(const float2 *src, double2 *dst, size_t count, int nsm, cudaStream_t s);
+// Reductions write `nvals` doubles per block into partials, then fold them in block order.
+int reduce_blocks(int nsm);
+void launch_diag_reduce(const float2 *rho, int n, double *partials, double *out, int nblocks,
+                        cudaStream_t s);
+void launch_purity(const float2 *rho, int n, double *partials, double *out, int nblocks,
+                   cudaStream_t s);
+void launch_project(float2 *rho, int n, int qubit, int m, float scale, int nsm, cudaStream_t s);
+void launch_partial_trace(const float2 *rho, const PTParams &p, double2 *out, int nsm,
+                          cudaStream_t s);
+int launches_per_reduce();
+
+// ------------------------------------------------------------------ queued operation
+struct QOp {
+    int kind;               // 0 = unitary, 1 = superoperator (channel)
+    int k;                  // number of qubits (1..5)
+    int qubits[5];
+    int ncontrols;
+    int controls[QCW_MAX_QUBITS];
+    std::vector<c128> m;    // unitary 2^k x 2^k, or superoperator 4^k x 4^k
+};
+
+struct FusedPlan;  // planner.cpp
+struct FusedRuntime;  // fused.cu
+
+}  // namespace qcw
+
+struct qcw_ctx {
+    int n = 0;
+    int dev = 0;
+    int nsm = 0;
+    float2 *rho = nullptr;
+    bool owns_rho = false;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    int mode = QCW_MODE_PLAIN;
+    int fuse_k = 0;
+    // reduction scratch: per-block partials and a small result block (+ pinned mirror)
+    double *d_partials = nullptr;
+    int red_blocks = 0;
+    double *d_result = nullptr;
+    double *h_result = nullptr;  // pinned, 64 doubles
+    // staging for complex128 <-> complex64 conversion
+    void *d_staging = nullptr;
+    size_t staging_bytes = 0;
+    // fused mode
+    std::vector<qcw::QOp> queue;
+    qcw::FusedRuntime *fused = nullptr;
+    // counters
+    long long launches = 0;
+    long long passes = 0;
+    long long timed_passes = 0;
+    double pass_ms = 0;
+    bool timing = false;
+};
+
+namespace qcw {
+// fused.cu / planner.cpp entry points used by the API layer
+qcw_status fused_flush(qcw_ctx *ctx);
+void fused_destroy(qcw_ctx *ctx);
+void fused_collect_timing(qcw_ctx *ctx);
+qcw_status plain_apply(qcw_ctx *c, const QOp &op);
+qcw_status set_error(qcw_status st, const std::string &msg);
+qcw_status cuda_error(cudaError_t e, const char *what);
+}  // namespace qcw

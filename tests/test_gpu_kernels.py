@@ -1,0 +1,228 @@
+"""GPU parity of every kernel against the CPU oracle, through the C ABI.
+
+Tolerance: max |delta rho| <= 1e-5 elementwise and |tr rho - 1| <= 1e-6 (FP32 complex
+state, FP64 oracle); measurement outcomes must be identical.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests._helpers import haar_unitary, random_rho
+
+pytestmark = pytest.mark.gpu
+
+ATOL = 1e-5
+TRACE_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def q():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1101_1785_gb300 as q
+
+    return q
+
+
+def _dens(q, rho, mode=None, k=0):
+    d = q.Density((rho.shape[0]).bit_length() - 1)
+    d.set_state(rho)
+    if mode is not None:
+        d.set_mode(mode, k)
+    return d
+
+
+def _close(got, want, atol=ATOL):
+    err = np.abs(got - want).max()
+    assert err <= atol, err
+    return err
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+def test_gate1_every_target(q, n):
+    rng = np.random.default_rng(100 + n)
+    for t in range(n):
+        u = haar_unitary(rng, 2)
+        rho = random_rho(rng, n)
+        d = _dens(q, rho)
+        d.apply_gate1(u, t)
+        _close(d.get_state(), oracle.apply_unitary(rho.copy(), u, [t]))
+        d.close()
+
+
+@pytest.mark.parametrize("n", [3, 6])
+def test_gate1_controls(q, n):
+    rng = np.random.default_rng(7)
+    cases = [(0, [n - 1]), (n - 1, [0]), (1, [0, 2])] if n > 3 else [(0, [2]), (2, [0, 1]), (1, [2])]
+    for t, ctrl in cases:
+        u = haar_unitary(rng, 2)
+        rho = random_rho(rng, n)
+        d = _dens(q, rho)
+        d.apply_gate1(u, t, ctrl)
+        _close(d.get_state(), oracle.apply_unitary(rho.copy(), u, [t], ctrl))
+        d.close()
+
+
+@pytest.mark.parametrize("n", [2, 3, 5])
+def test_gate2_every_ordered_pair(q, n):
+    rng = np.random.default_rng(200 + n)
+    for a in range(n):
+        for b in range(n):
+            if a == b:
+                continue
+            v = haar_unitary(rng, 4)
+            rho = random_rho(rng, n)
+            d = _dens(q, rho)
+            d.apply_gate2(v, a, b)
+            _close(d.get_state(), oracle.apply_unitary(rho.copy(), v, [a, b]))
+            d.close()
+
+
+def test_gate2_controls(q):
+    rng = np.random.default_rng(9)
+    n = 5
+    for (a, b), ctrl in (((0, 4), [2]), ((3, 1), [4, 0]), ((4, 2), [0])):
+        v = haar_unitary(rng, 4)
+        rho = random_rho(rng, n)
+        d = _dens(q, rho)
+        d.apply_gate2(v, a, b, ctrl)
+        _close(d.get_state(), oracle.apply_unitary(rho.copy(), v, [a, b], ctrl))
+        d.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_gate_k_dense(q, k):
+    rng = np.random.default_rng(300 + k)
+    n = 6
+    for _ in range(2):
+        qs = [int(x) for x in rng.permutation(n)[:k]]
+        u = haar_unitary(rng, 1 << k)
+        rho = random_rho(rng, n)
+        d = _dens(q, rho)
+        d.apply_gate(u, qs)
+        _close(d.get_state(), oracle.apply_unitary(rho.copy(), u, qs))
+        d.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 6])
+def test_kraus_one_qubit(q, n):
+    rng = np.random.default_rng(400 + n)
+    sets = [wl.kraus_ad(0.13), wl.kraus_pd(0.2), wl.kraus_depolarising(0.1),
+            np.stack([np.sqrt(0.3) * haar_unitary(rng, 2), np.sqrt(0.7) * haar_unitary(rng, 2)])]
+    for t in range(n):
+        ks = sets[t % len(sets)]
+        rho = random_rho(rng, n)
+        d = _dens(q, rho)
+        d.apply_kraus(ks, [t])
+        _close(d.get_state(), oracle.apply_kraus(rho.copy(), ks, [t]))
+        d.close()
+
+
+@pytest.mark.parametrize("n", [2, 3, 5])
+def test_kraus_two_qubit(q, n):
+    rng = np.random.default_rng(500 + n)
+    for a, b in [(0, n - 1), (n - 1, 0)] + ([(1, 2)] if n > 2 else []):
+        ks = np.stack([np.sqrt(w) * haar_unitary(rng, 4) for w in (0.5, 0.3, 0.2)])
+        rho = random_rho(rng, n)
+        d = _dens(q, rho)
+        d.apply_kraus(ks, [a, b])
+        _close(d.get_state(), oracle.apply_kraus(rho.copy(), ks, [a, b]))
+        d.close()
+
+
+@pytest.mark.parametrize("n", [1, 3, 6, 9])
+def test_readouts(q, n):
+    rng = np.random.default_rng(600 + n)
+    rho = random_rho(rng, n)
+    d = _dens(q, rho)
+    tr = d.trace()
+    assert abs(tr - oracle.trace(rho)) <= TRACE_TOL
+    assert abs(d.purity() - oracle.purity(rho)) <= 1e-6
+    np.testing.assert_allclose(d.probabilities(), oracle.probabilities(rho), atol=1e-6)
+    keeps = [[0], [n - 1], list(range(n))] + ([[0, n - 1], [1, n - 2]] if n >= 4 else [])
+    for keep in keeps:
+        _close(d.partial_trace(keep), oracle.partial_trace(rho, keep), atol=1e-6)
+    d.close()
+
+
+@pytest.mark.parametrize("n", [1, 4, 7])
+def test_measure(q, n):
+    rng = np.random.default_rng(700 + n)
+    rho = random_rho(rng, n)
+    for qb in sorted({0, n // 2, n - 1}):
+        for forced in (0, 1):
+            d = _dens(q, rho)
+            ref = rho.copy()
+            m_ref, p_ref = oracle.measure(ref, qb, forced)
+            m, p = d.measure(qb, forced)
+            assert m == m_ref and abs(p - p_ref) <= 1e-6
+            _close(d.get_state(), ref)
+            assert abs(d.trace() - 1) <= TRACE_TOL
+            d.close()
+        # u-driven outcome, u kept 1e-4 away from p0
+        p0 = 1 - oracle.probabilities(rho)[qb]
+        for u in (max(p0 - 0.05, 0.0), min(p0 + 0.05, 0.9999)):
+            if abs(u - p0) < 1e-4:
+                continue
+            d = _dens(q, rho)
+            ref = rho.copy()
+            m_ref, _ = oracle.measure(ref, qb, -1, u)
+            m, _ = d.measure(qb, -1, u)
+            assert m == m_ref
+            _close(d.get_state(), ref)
+            d.close()
+
+
+def test_measure_zero_probability(q):
+    d = q.Density(3)
+    before = d.get_state()
+    with pytest.raises(q.QcwError) as e:
+        d.measure(1, 1)
+    assert e.value.status == q.QCW_EZEROPROB
+    np.testing.assert_array_equal(d.get_state(), before)
+    d.close()
+
+
+def test_invalid_arguments_leave_state(q):
+    rng = np.random.default_rng(1)
+    rho = random_rho(rng, 3)
+    d = _dens(q, rho)
+    before = d.get_state()
+    for call in (lambda: d.apply_gate1(np.eye(2), 3),
+                 lambda: d.apply_gate1(np.eye(2), 0, [0]),
+                 lambda: d.apply_gate2(np.eye(4), 1, 1),
+                 lambda: d.apply_gate1(np.array([[np.nan, 0], [0, 1]]), 0),
+                 lambda: d.apply_kraus(np.zeros((0, 2, 2)), [0]),
+                 lambda: d.partial_trace([2, 2])):
+        with pytest.raises((q.QcwError, ValueError)):
+            call()
+    np.testing.assert_array_equal(d.get_state(), before)
+    d.close()
+
+
+def test_config1_plain(q):
+    c = wl.config1_circuit()
+    want = oracle.run_circuit(c)
+    d = q.run_circuit(c)
+    err = _close(d.get_state(), want)
+    assert abs(d.trace() - 1) <= TRACE_TOL
+    for forced in (0, 1):
+        ref = want.copy()
+        m_ref, p_ref = oracle.measure(ref, c.measure_qubit, forced)
+        dd = q.run_circuit(c)
+        m, p = dd.measure(c.measure_qubit, forced)
+        assert (m, round(p, 5)) == (m_ref, round(p_ref, 5)) or abs(p - p_ref) <= 1e-6
+        _close(dd.get_state(), ref)
+        dd.close()
+    print(f"config1 plain: max|drho| = {err:.2e}")
+    d.close()
+
+
+def test_determinism(q):
+    c = wl.random_circuit(8, 60, 5, "mixed", "adpd")
+    a = q.run_circuit(c).get_state()
+    b = q.run_circuit(c).get_state()
+    np.testing.assert_array_equal(a, b)
