@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the qcw density-matrix path on the 14-qubit noisy circuit.
+
+Workload (one "step"): a 14-qubit density matrix (16384 x 16384 complex64 on the device)
+starts in |0..0><0..0|; a seeded 1000-gate circuit (kinds uniform over H, X, Z, S, T,
+CNOT, Haar SU(2)) runs with amplitude damping (gamma = 0.01) and phase damping
+(lambda = 0.02) on every touched qubit after each gate, in the fused path (planner +
+fused-pass kernel, fusion width 5).  After every 100 gates the step reads trace and purity
+in FP64; at the end it reads the per-qubit probabilities, measures qubit 0 (u-driven
+projective measurement with renormalisation) and takes the partial trace over qubits 0, 1.
+
+Metric: gate-applications/s = gates per step x steps (x GPUs) / time.  One JSON line.
+``--impl reference`` times the CPU oracle on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gate-applications/s on 14-qubit noisy rho (HBM GB/s vs peak); req/s + p99 at 1e-5"
+UNIT = "gate-applications/s"
+N_QUBITS = 14
+N_GATES = 1000
+CHUNK = 100
+FUSE_K = 5
+U_MEASURE = 0.37
+PT_KEEP = [0, 1]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="qcw", choices=["qcw", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-gates", type=int, default=1, help="gates of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload():
+    import workloads as wl
+
+    c = wl.config3_circuit(n=N_QUBITS, ngates=N_GATES)
+    chunks = [c.gate_prefix(g).ops for g in range(0, N_GATES + 1, CHUNK)]
+    parts = [chunks[i + 1][len(chunks[i]):] for i in range(len(chunks) - 1)]
+    return c, parts
+
+
+def gpu_step(d, packed, host_rho_ptr=None):
+    """One pass of the whole path; returns the readouts (host FP64)."""
+    if host_rho_ptr is None:
+        d.reset()
+    else:
+        d.set_state_c64(host_rho_ptr)
+    tp = []
+    for p in packed:
+        d.apply_packed(p)
+        tp.append((d.trace(), d.purity()))
+    probs = d.probabilities()
+    m, pm = d.measure(0, -1, U_MEASURE)
+    pt = d.partial_trace(PT_KEEP)
+    return tp, probs, (m, pm), pt
+
+
+def d2h_bytes_per_step(n):
+    diag = (n + 2) * 8
+    return (N_GATES // CHUNK) * (diag + 8) + diag + diag + 16 * (4 ** len(PT_KEEP))
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("fused.cu", "planner.cpp", "qcw_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1101_1785_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """dram bytes per fused-pass launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "fused_pass_n14_traffic.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_hash") == kernel_hash():
+            return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_sample(ngates: int):
+    """Oracle on the first `ngates` gates (+ channels) of the same circuit; returns (gates/s, s, threads)."""
+    import oracle
+    import workloads as wl
+
+    c = wl.config3_circuit(n=N_QUBITS, ngates=N_GATES).gate_prefix(ngates)
+    threads = oracle.set_threads(0)
+    rho = oracle.initial_state(c)
+    t0 = time.perf_counter()
+    oracle.run_circuit(c, rho)
+    dt = time.perf_counter() - t0
+    del rho
+    return ngates / dt, dt, threads
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads  # noqa: F401
+
+    for _ in range(args.warmup):
+        oracle_sample(args.cpu_gates)
+    t0 = time.perf_counter()
+    total = 0.0
+    threads = 0
+    for _ in range(args.steps):
+        _, dt, threads = oracle_sample(args.cpu_gates)
+        total += dt
+    elapsed = time.perf_counter() - t0
+    value = args.cpu_gates * args.steps / total
+    sample = (f"first {args.cpu_gates} gate(s) of the 1000-gate 14-qubit circuit with their AD+PD "
+              f"channels, complex128 oracle, per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": "14-qubit noisy density matrix, 1000-gate seeded circuit, AD(0.01)+PD(0.02)",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": elapsed,
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+        __graft_entry__.build()  # no-op once rank 0 compiled; also loads the module
+    import paper_1101_1785_gb300 as q
+
+    circuit, parts = make_workload()
+    packed = [q.PackedOps(p) for p in parts]
+    d = q.Density(N_QUBITS)
+    d.set_mode(q.QCW_MODE_FUSED, FUSE_K)
+    rho_ptr, stream_ptr = d.device_state()
+    ext = torch.cuda.ExternalStream(stream_ptr)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    for _ in range(max(3, args.warmup)):
+        gpu_step(d, packed)
+    barrier()
+    d.stats_reset()
+    d.enable_pass_timing(True)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    phys = int(vis.split(",")[local]) if vis and vis.split(",")[local].strip().isdigit() else local
+    sampler = ClockSampler(phys)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(ext)
+    for _ in range(args.steps):
+        out = gpu_step(d, packed)
+    ev1.record(ext)
+    barrier()
+    clocks = sampler.stop()
+    d.enable_pass_timing(False)
+    st = d.stats()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    tp, probs, meas, pt = out
+    max_tr_err = max(abs(x[0] - 1) for x in tp)
+
+    # ---- end to end: rho_0 uploaded from pinned host memory every step, readouts to host
+    host = torch.zeros(2 * (4 ** N_QUBITS), dtype=torch.float32).pin_memory()
+    host[0] = 1.0
+    for _ in range(2):
+        gpu_step(d, packed, host.data_ptr())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        gpu_step(d, packed, host.data_ptr())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    d.close()
+
+    total_gates = N_GATES * args.steps * world
+    value = total_gates / (ms / 1e3)
+    e2e_value = total_gates / e2e_s
+
+    peaks, peak_kind = load_peaks()
+    per_launch_bytes = 16 * (4 ** N_QUBITS)
+    avg_ms = st["fused_pass_ms"] / max(1, st["timed_passes"])
+    achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
+    hbm = float(peaks["hbm_gbs"])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, threads = oracle_sample(args.cpu_gates)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {args.cpu_gates} gate(s) of the same circuit with their AD+PD channels "
+                         f"on the complex128 oracle ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "14-qubit noisy density matrix (16384 x 16384 complex64), seeded "
+                                   "1000-gate circuit {H,X,Z,S,T,CNOT,Haar}, AD(0.01)+PD(0.02) per "
+                                   "touched qubit, fused width 5, FP64 trace+purity every 100 gates, "
+                                   "probabilities, measurement, partial trace",
+                       "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2 GiB rho)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": recorded_traffic(),
+                         "peak_kind": peak_kind, "kernel": "k_fused_pass",
+                         "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (4 ** N_QUBITS),
+                    "d2h_bytes_per_step": d2h_bytes_per_step(N_QUBITS)},
+            "gpu_launches": st["launches"],
+            "fused_passes_per_step": st["fused_passes"] / args.steps,
+            "clocks": clocks,
+            "checks": {"max_abs_trace_err": max_tr_err, "final_purity": tp[-1][1],
+                       "outcome_q0": meas[0], "p_outcome": meas[1]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -128,6 +128,23 @@ QCW_API qcw_status qcw_apply_gate(qcw_ctx *ctx, const double *u, const int *qubi
 QCW_API qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkraus, const int *qubits,
                            int k);
 
+/* One element of a circuit handed over in a single call (qcw_apply_ops). */
+#define QCW_OP_GATE 0
+#define QCW_OP_KRAUS 1
+typedef struct {
+    int kind;           /* QCW_OP_GATE or QCW_OP_KRAUS */
+    int k;              /* qubits: 1..QCW_MAX_GATE_QUBITS for a gate, 1..2 for Kraus */
+    int qubits[QCW_MAX_GATE_QUBITS]; /* first k entries used, paper order */
+    int nkraus;         /* Kraus operators (1..16) for QCW_OP_KRAUS; ignored for gates */
+    long long offset;   /* index, in doubles, of the op's first matrix in `matrices` */
+} qcw_op;
+
+/* Apply nops operations in order, exactly as the matching sequence of qcw_apply_gate /
+ * qcw_apply_kraus calls would (gates: one 2^k x 2^k matrix at matrices + offset; Kraus:
+ * nkraus matrices one after another).  Every op is checked before any is applied, so on
+ * QCW_EINVAL nothing has changed.  Both arrays may be freed when the call returns. */
+QCW_API qcw_status qcw_apply_ops(qcw_ctx *ctx, const qcw_op *ops, int nops, const double *matrices);
+
 /* Launch queued fused work (no-op in plain mode). */
 QCW_API qcw_status qcw_flush(qcw_ctx *ctx);
 

@@ -15,6 +15,8 @@ from ._binding import (  # noqa: F401
     QCW_OK,
     SIGNATURES,
     Density,
+    PackedOps,
+    QcwOp,
     QcwError,
     lib,
     run_circuit,

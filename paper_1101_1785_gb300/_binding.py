@@ -49,6 +49,7 @@ SIGNATURES = {
     "qcw_apply_gate2": (I, [P, P, I, I, P, I]),
     "qcw_apply_gate": (I, [P, P, P, I]),
     "qcw_apply_kraus": (I, [P, P, I, P, I]),
+    "qcw_apply_ops": (I, [P, P, I, P]),
     "qcw_flush": (I, [P]),
     "qcw_sync": (I, [P]),
     "qcw_trace": (I, [P, PD, PD]),
@@ -62,6 +63,43 @@ SIGNATURES = {
     "qcw_stats_reset": (I, [P]),
     "qcw_enable_pass_timing": (I, [P, I]),
 }
+
+
+class QcwOp(ctypes.Structure):
+    """Mirror of qcw_op (include/qcw.h)."""
+
+    _fields_ = [("kind", ctypes.c_int), ("k", ctypes.c_int), ("qubits", ctypes.c_int * 5),
+                ("nkraus", ctypes.c_int), ("offset", ctypes.c_longlong)]
+
+
+QCW_OP_GATE, QCW_OP_KRAUS = 0, 1
+
+
+class PackedOps:
+    """A circuit's op list packed once into the qcw_op array + matrix buffer of qcw_apply_ops."""
+
+    def __init__(self, ops):
+        ops = list(ops)
+        self.n_ops = len(ops)
+        self.descs = (QcwOp * max(1, len(ops)))()
+        mats = []
+        off = 0
+        for i, op in enumerate(ops):
+            d = self.descs[i]
+            d.kind = QCW_OP_GATE if op.kind == "gate" else QCW_OP_KRAUS
+            d.k = len(op.qubits)
+            for j, qb in enumerate(op.qubits):
+                d.qubits[j] = int(qb)
+            m = np.ascontiguousarray(np.asarray(op.mats if op.kind != "gate" else op.mats[0], dtype=np.complex128))
+            d.nkraus = int(op.mats.shape[0]) if op.kind != "gate" else 1
+            d.offset = off
+            mats.append(m.reshape(-1))
+            off += 2 * m.size
+        self.matrices = np.ascontiguousarray(np.concatenate(mats) if mats else np.zeros(1, np.complex128))
+
+    @property
+    def nbytes(self) -> int:
+        return ctypes.sizeof(QcwOp) * self.n_ops + self.matrices.nbytes
 
 
 class QcwError(RuntimeError):
@@ -206,6 +244,11 @@ class Density:
                 self.apply_gate(op.mats[0], op.qubits)
         else:
             self.apply_kraus(op.mats, op.qubits)
+
+    def apply_packed(self, packed: "PackedOps"):
+        """Apply a PackedOps list in one C call (qcw_apply_ops)."""
+        check(lib().qcw_apply_ops(self.h, ctypes.cast(packed.descs, P), packed.n_ops,
+                                  packed.matrices.ctypes.data_as(P)), "qcw_apply_ops")
 
     def flush(self):
         check(lib().qcw_flush(self.h), "qcw_flush")

@@ -196,13 +196,9 @@ qcw_status plain_apply(qcw_ctx *c, const QOp &op)
 
 static qcw_status submit(qcw_ctx *c, QOp &&op)
 {
-    if (c->mode == QCW_MODE_FUSED && op.ncontrols == 0) {
+    if (c->mode == QCW_MODE_FUSED) {
         c->queue.push_back(std::move(op));
         return QCW_OK;
-    }
-    if (c->mode == QCW_MODE_FUSED) {
-        qcw_status st = fused_flush(c);
-        if (st) return st;
     }
     return plain_apply(c, op);
 }
@@ -458,6 +454,48 @@ extern "C" qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkr
     op.ncontrols = 0;
     op.m = kraus_superop(to_c128(kraus, cnt), nkraus, k);
     return submit(ctx, std::move(op));
+}
+
+extern "C" qcw_status qcw_apply_ops(qcw_ctx *ctx, const qcw_op *ops, int nops, const double *matrices)
+{
+    CHECK_CTX(ctx);
+    if (nops < 0 || (nops > 0 && (!ops || !matrices))) return set_error(QCW_EINVAL, "bad op list");
+    for (int i = 0; i < nops; i++) {  // validate everything first: all or nothing
+        const qcw_op &o = ops[i];
+        if (o.offset < 0) return set_error(QCW_EINVAL, "negative matrix offset");
+        if (o.kind == QCW_OP_GATE) {
+            if (o.k < 1 || o.k > QCW_MAX_GATE_QUBITS) return set_error(QCW_EINVAL, "k out of range");
+            qcw_status st = check_qubits(ctx->n, o.qubits, o.k, nullptr, 0);
+            if (st) return st;
+            if (!all_finite(matrices + o.offset, (size_t)2 << (2 * o.k)))
+                return set_error(QCW_EINVAL, "non-finite matrix entry");
+        } else if (o.kind == QCW_OP_KRAUS) {
+            if (o.k < 1 || o.k > 2) return set_error(QCW_EINVAL, "channels act on 1 or 2 qubits");
+            if (o.nkraus < 1 || o.nkraus > 16) return set_error(QCW_EINVAL, "nkraus out of range");
+            qcw_status st = check_qubits(ctx->n, o.qubits, o.k, nullptr, 0);
+            if (st) return st;
+            if (!all_finite(matrices + o.offset, ((size_t)2 * o.nkraus) << (2 * o.k)))
+                return set_error(QCW_EINVAL, "non-finite matrix entry");
+        } else {
+            return set_error(QCW_EINVAL, "bad op kind");
+        }
+    }
+    for (int i = 0; i < nops; i++) {
+        const qcw_op &o = ops[i];
+        QOp op;
+        op.kind = o.kind == QCW_OP_GATE ? 0 : 1;
+        op.k = o.k;
+        for (int j = 0; j < o.k; j++) op.qubits[j] = o.qubits[j];
+        op.ncontrols = 0;
+        if (o.kind == QCW_OP_GATE) {
+            op.m = to_c128(matrices + o.offset, (size_t)1 << (2 * o.k));
+        } else {
+            op.m = kraus_superop(to_c128(matrices + o.offset, (size_t)o.nkraus << (2 * o.k)), o.nkraus, o.k);
+        }
+        qcw_status st = submit(ctx, std::move(op));
+        if (st) return st;
+    }
+    return QCW_OK;
 }
 
 extern "C" qcw_status qcw_flush(qcw_ctx *ctx)

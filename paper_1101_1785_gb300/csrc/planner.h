@@ -1,0 +1,31 @@
+// Fusion planner: packs a queue of one- and two-qubit operations (unitaries and channel
+// superoperators) into passes over rho, each touching at most k qubits, and each pass into
+// phases of at most two qubits whose operations are composed into one superoperator.
+#pragma once
+#include <complex>
+#include <vector>
+
+#include "qcw_internal.h"
+
+namespace qcw {
+
+struct PhasePlan {
+    int nq;                 // 1 or 2
+    int qa, qb;             // phase qubits (qb = -1 when nq == 1)
+    std::vector<c128> S;    // composed superoperator, 4x4 (nq = 1) or 16x16 (nq = 2)
+    int nops;               // operations folded into S
+};
+
+struct PassPlan {
+    std::vector<int> Q;           // qubits the pass touches (ascending)
+    std::vector<PhasePlan> phases;
+    int nops;
+};
+
+// Superoperator of a unitary on k qubits: S[(r',c'), (r,c)] = U[r', r] conj(U[c', c]).
+std::vector<c128> unitary_superop(const std::vector<c128> &u, int k);
+
+// Plan ops[begin, end) (all with k <= 2 and no controls) for an n-qubit register.
+std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, size_t end, int n, int kmax);
+
+}  // namespace qcw

@@ -1,0 +1,174 @@
+"""GPU parity of the fused path (planner + fused-pass kernel) against the CPU oracle.
+
+Tolerance as everywhere: max |delta rho| <= 1e-5, |tr rho - 1| <= 1e-6 (FP32 state vs the
+FP64 oracle).  The 14-qubit cases run in the launch configuration the benchmark times
+(fusion width 5, 2^13-element tiles).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests._helpers import haar_unitary, random_rho
+
+pytestmark = pytest.mark.gpu
+
+ATOL = 1e-5
+TRACE_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def q():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1101_1785_gb300 as q
+
+    return q
+
+
+def _run(q, c, mode, k=0, rho0=None):
+    d = q.Density(c.n)
+    d.set_mode(mode, k)
+    if rho0 is not None:
+        d.set_state(rho0)
+    elif c.init == "matrix":
+        d.set_state(c.rho0)
+    for op in c.ops:
+        d.apply_op(op)
+    return d
+
+
+@pytest.mark.parametrize("n,k", [(2, 2), (3, 2), (3, 3), (4, 4), (5, 3), (6, 5), (7, 4), (8, 5)])
+def test_fused_random_noisy_circuits(q, n, k):
+    for noise, seed in (("adpd", 1), ("dep", 2), ("none", 3)):
+        c = wl.random_circuit(n, 50, 1000 * n + seed, "mixed", noise)
+        rho0 = random_rho(np.random.default_rng(seed + n), n)
+        want = oracle.run_circuit(c, rho0.copy())
+        d = _run(q, c, q.QCW_MODE_FUSED, k, rho0)
+        got = d.get_state()
+        err = np.abs(got - want).max()
+        assert err <= ATOL, (noise, err)
+        assert abs(d.trace() - oracle.trace(want)) <= TRACE_TOL
+        d.close()
+
+
+def test_fused_two_qubit_channels_and_dense_gates(q):
+    rng = np.random.default_rng(77)
+    n = 6
+    rho = random_rho(rng, n)
+    want = rho.copy()
+    d = q.Density(n)
+    d.set_state(rho)
+    d.set_mode(q.QCW_MODE_FUSED, 4)
+    for step in range(12):
+        a, b = [int(x) for x in rng.permutation(n)[:2]]
+        ks = np.stack([np.sqrt(w) * haar_unitary(rng, 4) for w in (0.6, 0.4)])
+        d.apply_kraus(ks, [a, b])
+        oracle.apply_kraus(want, ks, [a, b])
+        u = haar_unitary(rng, 2)
+        d.apply_gate1(u, (a + step) % n)
+        oracle.apply_unitary(want, u, [(a + step) % n])
+        if step % 4 == 0:  # dense 3-qubit gate: a barrier for the planner
+            qs = [int(x) for x in rng.permutation(n)[:3]]
+            u3 = haar_unitary(rng, 8)
+            d.apply_gate(u3, qs)
+            oracle.apply_unitary(want, u3, qs)
+        if step % 3 == 0:  # controlled gates: 1 + 1 is lowered, 1 + 2 runs on its own
+            u = haar_unitary(rng, 2)
+            d.apply_gate1(u, b, [a])
+            oracle.apply_unitary(want, u, [b], [a])
+            c2 = [x for x in range(n) if x not in (a, b)][:2]
+            d.apply_gate1(u, b, c2)
+            oracle.apply_unitary(want, u, [b], c2)
+    assert np.abs(d.get_state() - want).max() <= ATOL
+    d.close()
+
+
+def test_fused_matches_plain_and_is_deterministic(q):
+    c = wl.random_circuit(9, 200, 4242, "mixed", "adpd")
+    a = _run(q, c, q.QCW_MODE_PLAIN).get_state()
+    f1 = _run(q, c, q.QCW_MODE_FUSED, 5).get_state()
+    f2 = _run(q, c, q.QCW_MODE_FUSED, 5).get_state()
+    assert np.abs(a - f1).max() <= 1e-6
+    np.testing.assert_array_equal(f1, f2)
+
+
+def test_config1_fused_with_measurement(q):
+    c = wl.config1_circuit()
+    want = oracle.run_circuit(c)
+    for forced in (0, 1):
+        d = _run(q, c, q.QCW_MODE_FUSED, 4)
+        assert np.abs(d.get_state() - want).max() <= ATOL
+        assert abs(d.trace() - 1) <= TRACE_TOL
+        ref = want.copy()
+        m_ref, p_ref = oracle.measure(ref, 0, forced)
+        m, p = d.measure(0, forced)
+        assert m == m_ref and abs(p - p_ref) <= 1e-6
+        assert np.abs(d.get_state() - ref).max() <= ATOL
+        d.close()
+
+
+def test_plan_cache_reuse_and_miss(q):
+    c1 = wl.random_circuit(7, 80, 11, "mixed", "adpd")
+    c2 = wl.random_circuit(7, 80, 12, "mixed", "adpd")
+    d = q.Density(7)
+    d.set_mode(q.QCW_MODE_FUSED, 5)
+    for c in (c1, c2, c1, c2):
+        d.reset()
+        for op in c.ops:
+            d.apply_op(op)
+        np.testing.assert_allclose(d.get_state(), oracle.run_circuit(c), atol=ATOL, rtol=0)
+    d.close()
+
+
+def test_config2_prefix_n12_fused_and_plain(q):
+    c = wl.config2_circuit()
+    pre = c.gate_prefix(30)
+    want = oracle.run_circuit(pre)
+    for mode in (q.QCW_MODE_PLAIN, q.QCW_MODE_FUSED):
+        d = _run(q, pre, mode, 5)
+        err = np.abs(d.get_state() - want).max()
+        assert err <= ATOL, err
+        assert abs(d.trace() - 1) <= TRACE_TOL
+        d.close()
+
+
+def test_full_size_n14_embedded_subsystem(q):
+    """n = 14 in the benchmark's launch configuration, on a circuit confined to five qubits
+    spread over the register: rho = rho_S (x) |0><0| on the rest, with rho_S from the oracle."""
+    n, S = 14, [0, 3, 7, 12, 13]
+    small = wl.random_circuit(5, 120, 314, "mixed", "adpd")
+    want_s = oracle.run_circuit(small)
+    d = q.Density(n)
+    d.set_mode(q.QCW_MODE_FUSED, 5)
+    for op in small.ops:
+        mapped = [S[x] for x in op.qubits]
+        if op.kind == "gate":
+            if op.k == 1:
+                d.apply_gate1(op.mats[0], mapped[0])
+            else:
+                d.apply_gate2(op.mats[0], mapped[0], mapped[1])
+        else:
+            d.apply_kraus(op.mats, mapped)
+    got = d.get_state()
+    assert abs(d.trace() - 1) <= TRACE_TOL
+    d.close()
+    t = got.reshape([2] * (2 * n))
+    idx = tuple(slice(None) if (ax % n) in S else 0 for ax in range(2 * n))
+    block = t[idx].reshape(32, 32)
+    assert np.abs(block - want_s).max() <= ATOL
+    t[idx] = 0
+    assert np.abs(got).max() == 0.0
+
+
+def test_full_size_n14_config3_prefix(q):
+    """First three gates of the 14-qubit benchmark circuit, fused k = 5, against the oracle."""
+    c = wl.config3_circuit().gate_prefix(3)
+    want = oracle.run_circuit(c)
+    d = _run(q, c, q.QCW_MODE_FUSED, 5)
+    got = d.get_state()
+    assert np.abs(got - want).max() <= ATOL
+    assert abs(d.trace() - 1) <= TRACE_TOL
+    d.close()
