@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--impl", default="qcw", choices=["qcw", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-gates", type=int, default=1, help="gates of the oracle sample")
+    ap.add_argument("--qubits", type=int, default=N_QUBITS,
+                    help="register size (14 is the benchmark; smaller sizes are for profiling)")
     return ap.parse_args()
 
 
@@ -106,10 +108,10 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- workload
-def make_workload():
+def make_workload(n):
     import workloads as wl
 
-    c = wl.config3_circuit(n=N_QUBITS, ngates=N_GATES)
+    c = wl.config3_circuit(n=n, ngates=N_GATES)
     chunks = [c.gate_prefix(g).ops for g in range(0, N_GATES + 1, CHUNK)]
     parts = [chunks[i + 1][len(chunks[i]):] for i in range(len(chunks) - 1)]
     return c, parts
@@ -230,9 +232,10 @@ def run_ours(args):
         __graft_entry__.build()  # no-op once rank 0 compiled; also loads the module
     import paper_1101_1785_gb300 as q
 
-    circuit, parts = make_workload()
+    nq = args.qubits
+    circuit, parts = make_workload(nq)
     packed = [q.PackedOps(p) for p in parts]
-    d = q.Density(N_QUBITS)
+    d = q.Density(nq)
     d.set_mode(q.QCW_MODE_FUSED, FUSE_K)
     rho_ptr, stream_ptr = d.device_state()
     ext = torch.cuda.ExternalStream(stream_ptr)
@@ -270,7 +273,7 @@ def run_ours(args):
     max_tr_err = max(abs(x[0] - 1) for x in tp)
 
     # ---- end to end: rho_0 uploaded from pinned host memory every step, readouts to host
-    host = torch.zeros(2 * (4 ** N_QUBITS), dtype=torch.float32).pin_memory()
+    host = torch.zeros(2 * (4 ** nq), dtype=torch.float32).pin_memory()
     host[0] = 1.0
     for _ in range(2):
         gpu_step(d, packed, host.data_ptr())
@@ -291,13 +294,13 @@ def run_ours(args):
     e2e_value = total_gates / e2e_s
 
     peaks, peak_kind = load_peaks()
-    per_launch_bytes = 16 * (4 ** N_QUBITS)
+    per_launch_bytes = 16 * (4 ** nq)
     avg_ms = st["fused_pass_ms"] / max(1, st["timed_passes"])
     achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
     hbm = float(peaks["hbm_gbs"])
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and nq == N_QUBITS:
         v, dt, threads = oracle_sample(args.cpu_gates)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"first {args.cpu_gates} gate(s) of the same circuit with their AD+PD channels "
@@ -312,14 +315,15 @@ def run_ours(args):
                                    "1000-gate circuit {H,X,Z,S,T,CNOT,Haar}, AD(0.01)+PD(0.02) per "
                                    "touched qubit, fused width 5, FP64 trace+purity every 100 gates, "
                                    "probabilities, measurement, partial trace",
-                       "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2 GiB rho)"},
+                       "qubits": nq, "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 ({8 * 4 ** nq / 2**20:.0f} MiB rho vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": recorded_traffic(),
                          "peak_kind": peak_kind, "kernel": "k_fused_pass",
                          "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (4 ** N_QUBITS),
-                    "d2h_bytes_per_step": d2h_bytes_per_step(N_QUBITS)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (4 ** nq),
+                    "d2h_bytes_per_step": d2h_bytes_per_step(nq)},
             "gpu_launches": st["launches"],
             "fused_passes_per_step": st["fused_passes"] / args.steps,
             "clocks": clocks,
