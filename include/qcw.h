@@ -174,6 +174,31 @@ QCW_API qcw_status qcw_measure(qcw_ctx *ctx, int qubit, int forced, double u, in
  * bit of a.  out_c128 receives 2 * 4^nkeep doubles (subsystem states of Sec. 5.2.3). */
 QCW_API qcw_status qcw_partial_trace(qcw_ctx *ctx, const int *keep, int nkeep, double *out_c128);
 
+/* Size of the fixed result array used by qcw_partial_trace_static: 4^6 complex128 entries. */
+#define QCW_PT_STATIC_MAX_ENTRIES 4096
+
+/* Partial trace that allocates nothing (the paper has no counterpart; this is a service for
+ * callers that must not allocate device memory).  Some callers cannot call cudaMalloc: while
+ * any thread of the process captures a CUDA graph in global mode, cudaMalloc and cudaFree are
+ * not allowed; an application whose allocator already holds the whole device budget has no
+ * memory to give; and cudaFree synchronises the device, which a latency-critical loop cannot
+ * afford.  qcw_partial_trace takes its device result buffer from cudaMallocAsync; this variant
+ * instead writes into one array of QCW_PT_STATIC_MAX_ENTRIES complex128 values (64 KiB) that
+ * lives in device memory as part of the library, on every GPU that loads it, until exit.
+ *
+ * dev_rho: caller's device rho of nqubits (row-major complex64, the layout above); cuda_stream:
+ * a cudaStream_t (NULL = legacy default stream) on the current device; keep / nkeep / out_c128
+ * as for qcw_partial_trace (host output of 2 * 4^nkeep doubles).  nkeep above 6 returns
+ * QCW_EINVAL ("keeps at most 6 qubits").  The call waits for its stream before returning.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture starts.  The kernel
+ * writes every result entry, so nothing has to start at zero; the array keeps the last call's
+ * contents.  All calls share the one array: calls whose work overlaps on the GPU (different
+ * streams, or threads racing on one device) race on it and must be serialised by the caller. */
+QCW_API qcw_status qcw_partial_trace_static(const void *dev_rho, int nqubits, const int *keep, int nkeep,
+                                    void *cuda_stream, double *out_c128);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Message of the last failure on this thread ("" if none). */

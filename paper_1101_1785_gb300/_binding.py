@@ -57,6 +57,7 @@ SIGNATURES = {
     "qcw_probabilities": (I, [P, P]),
     "qcw_measure": (I, [P, I, I, D, PI, PD]),
     "qcw_partial_trace": (I, [P, P, I, P]),
+    "qcw_partial_trace_static": (I, [P, I, P, I, P, P]),
     "qcw_last_error": (ctypes.c_char_p, []),
     "qcw_strerror": (ctypes.c_char_p, [I]),
     "qcw_stats": (I, [P, PLL, PLL, PD, PLL]),
