@@ -199,6 +199,79 @@ QCW_API qcw_status qcw_partial_trace(qcw_ctx *ctx, const int *keep, int nkeep, d
 QCW_API qcw_status qcw_partial_trace_static(const void *dev_rho, int nqubits, const int *keep, int nkeep,
                                     void *cuda_stream, double *out_c128);
 
+/* ---------------------------------------------------------------- batched circuits */
+
+/* Many independent circuits in one launch: the paper's multiverse runs independent paths on
+ * separate processors (Sec. 5.1, Sec. 5.2.1); here they share one GPU.  Circuit j has
+ * nqubits[j] (1..QCW_MAX_QUBITS) qubits, starts in |0..0><0..0| and applies
+ * ops[op_begin[j] .. op_begin[j+1]) (1- and 2-qubit gates and Kraus channels, matrices as in
+ * qcw_apply_ops).  fuse_k (0 = chosen per circuit by the cost model, else 2..5) bounds the
+ * qubits of a fused pass.  Creation plans every circuit, allocates one device arena for all
+ * states and captures the whole run (one persistent kernel) in a CUDA graph on cuda_stream
+ * (NULL = legacy default stream).  All arrays are copied; the caller may free them on return. */
+typedef struct qcw_batch qcw_batch;
+QCW_API qcw_status qcw_batch_create(int ncirc, const int *nqubits, const long long *op_begin, const qcw_op *ops,
+                                    const double *matrices, int fuse_k, void *cuda_stream, qcw_batch **out);
+/* Launch the captured graph (asynchronous).  Each run starts every circuit from |0..0><0..0|. */
+QCW_API qcw_status qcw_batch_run(qcw_batch *b);
+/* Wait for the last run, at most timeout_s seconds (< 0: no limit): QCW_ETIMEOUT if it is
+ * still running, or if a work item's bounded dependency wait ran out inside the kernel. */
+QCW_API qcw_status qcw_batch_wait(qcw_batch *b, double timeout_s);
+/* Readouts of the last run (waits): p1 gets sum_j nqubits[j] values (circuit order, per qubit
+ * P(q = 1)), purity and trace one value per circuit (FP64).  Any pointer may be NULL. */
+QCW_API qcw_status qcw_batch_results(qcw_batch *b, double *p1, double *purity, double *trace);
+/* Final rho of one circuit as host complex128 (2 * 4^n doubles). */
+QCW_API qcw_status qcw_batch_get_state(qcw_batch *b, int circuit, double *rho_c128);
+/* Work items, fused passes, phases and modeled SM-seconds of one run. */
+QCW_API qcw_status qcw_batch_info(qcw_batch *b, long long *items, long long *passes, long long *phases,
+                                  double *modeled_sm_s);
+/* Diagnostics: bound every in-kernel dependency wait to `polls` polls (~128 ns each) and, when
+ * stall_item >= 0, make that item wait on a counter that is never set (a host-side injected
+ * fault: the wait runs out, the run ends with QCW_ETIMEOUT from qcw_batch_wait, the context
+ * stays usable).  stall_item = -1 restores the normal item list. */
+QCW_API qcw_status qcw_batch_set_wait_limit(qcw_batch *b, long long polls, int stall_item);
+QCW_API qcw_status qcw_batch_destroy(qcw_batch *b);
+
+/* ---------------------------------------------------------------- serving loop */
+
+/* Continuous batching of circuit requests.  A request (1..13 qubits, op list as for
+ * qcw_apply_ops) is planned when submitted and waits in FIFO order; it is admitted while the
+ * summed footprint 16 * 4^n bytes of live requests stays within budget_bytes (at most
+ * max_live at once); its rho stays on the device until it finishes.  Each qcw_server_step
+ * waits (boundedly) for the previous step, harvests finished requests, admits waiting ones
+ * and launches one engine kernel over every live request: requests whose rho fits one tile
+ * finish inside the step, larger ones advance by up to passes_per_step fused passes.
+ * Requests submitted while a step runs join the next one.  A request's result does not depend
+ * on which other requests share its steps. */
+typedef struct qcw_server qcw_server;
+typedef struct {
+    long long id;
+    int nqubits;
+    int status;        /* QCW_OK, or QCW_ETIMEOUT if a wait in its last step ran out */
+    double trace;      /* Re Tr rho */
+    double purity;     /* sum |rho_ij|^2 */
+    double p1[QCW_MAX_QUBITS]; /* P(q = 1) for q < nqubits */
+    double t_submit, t_done;   /* host steady-clock seconds */
+} qcw_result;
+QCW_API qcw_status qcw_server_create(size_t budget_bytes, int max_live, int passes_per_step, void *cuda_stream,
+                                     qcw_server **out);
+/* Plan and queue one request; *id receives its id.  Thread-safe with respect to qcw_server_step. */
+QCW_API qcw_status qcw_server_submit(qcw_server *s, int nqubits, const qcw_op *ops, int nops, const double *matrices,
+                                     long long *id);
+/* One engine step (returns once the next step is launched; *launched_items may be NULL). */
+QCW_API qcw_status qcw_server_step(qcw_server *s, int *launched_items);
+/* Step until nothing waits or runs, at most timeout_s seconds (< 0: the server's wait limit per step). */
+QCW_API qcw_status qcw_server_drain(qcw_server *s, double timeout_s);
+/* Move up to max finished results (in completion order) to out; *count receives how many. */
+QCW_API qcw_status qcw_server_poll(qcw_server *s, qcw_result *out, int max, int *count);
+QCW_API qcw_status qcw_server_stats(qcw_server *s, long long *waiting, long long *live, long long *completed,
+                                    long long *bytes_in_use);
+/* Diagnostics: host wait limit per step (seconds), in-kernel dependency-wait bound (polls), and
+ * with stall_next_step != 0 one item of the next step waits on a counter nothing sets (the step
+ * then reports QCW_ETIMEOUT; the server stays usable). */
+QCW_API qcw_status qcw_server_set_limits(qcw_server *s, double wait_limit_s, long long polls, int stall_next_step);
+QCW_API qcw_status qcw_server_destroy(qcw_server *s);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Message of the last failure on this thread ("" if none). */

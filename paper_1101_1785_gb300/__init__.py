@@ -14,7 +14,10 @@ from ._binding import (  # noqa: F401
     QCW_MODE_PLAIN,
     QCW_OK,
     SIGNATURES,
+    Batch,
     Density,
+    Server,
+    QcwResult,
     PackedOps,
     QcwOp,
     QcwError,

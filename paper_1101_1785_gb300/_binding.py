@@ -58,6 +58,22 @@ SIGNATURES = {
     "qcw_measure": (I, [P, I, I, D, PI, PD]),
     "qcw_partial_trace": (I, [P, P, I, P]),
     "qcw_partial_trace_static": (I, [P, I, P, I, P, P]),
+    "qcw_batch_create": (I, [I, P, P, P, P, I, P, PP]),
+    "qcw_batch_run": (I, [P]),
+    "qcw_batch_wait": (I, [P, D]),
+    "qcw_batch_results": (I, [P, P, P, P]),
+    "qcw_batch_get_state": (I, [P, I, P]),
+    "qcw_batch_info": (I, [P, PLL, PLL, PLL, PD]),
+    "qcw_batch_set_wait_limit": (I, [P, LL, I]),
+    "qcw_batch_destroy": (I, [P]),
+    "qcw_server_create": (I, [ctypes.c_size_t, I, I, P, PP]),
+    "qcw_server_submit": (I, [P, I, P, I, P, PLL]),
+    "qcw_server_step": (I, [P, PI]),
+    "qcw_server_drain": (I, [P, D]),
+    "qcw_server_poll": (I, [P, P, I, PI]),
+    "qcw_server_stats": (I, [P, PLL, PLL, PLL, PLL]),
+    "qcw_server_set_limits": (I, [P, D, LL, I]),
+    "qcw_server_destroy": (I, [P]),
     "qcw_last_error": (ctypes.c_char_p, []),
     "qcw_strerror": (ctypes.c_char_p, [I]),
     "qcw_stats": (I, [P, PLL, PLL, PD, PLL]),
@@ -310,3 +326,149 @@ def run_circuit(circuit, dens: Density | None = None, ops=None) -> Density:
     for op in (circuit.ops if ops is None else ops):
         d.apply_op(op)
     return d
+
+
+class QcwResult(ctypes.Structure):
+    """Mirror of qcw_result (include/qcw.h)."""
+
+    _fields_ = [("id", ctypes.c_longlong), ("nqubits", ctypes.c_int), ("status", ctypes.c_int),
+                ("trace", ctypes.c_double), ("purity", ctypes.c_double), ("p1", ctypes.c_double * QCW_MAX_QUBITS),
+                ("t_submit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class Batch:
+    """qcw_batch_*: many circuits (workloads.Circuit, starting from |0..0>) in one graph launch."""
+
+    def __init__(self, circuits, fuse_k: int = 0, stream: int = 0):
+        circuits = list(circuits)
+        packs = [PackedOps(c.ops) for c in circuits]
+        nq = np.asarray([c.n for c in circuits], dtype=np.int32)
+        begin = np.zeros(len(circuits) + 1, dtype=np.int64)
+        total = sum(p.n_ops for p in packs)
+        descs = (QcwOp * max(1, total))()
+        mats = []
+        k = 0
+        moff = 0
+        for j, p in enumerate(packs):
+            begin[j] = k
+            for i in range(p.n_ops):
+                descs[k] = p.descs[i]
+                descs[k].offset = p.descs[i].offset + moff
+                k += 1
+            mats.append(p.matrices)
+            moff += 2 * p.matrices.size
+        begin[len(circuits)] = k
+        self.matrices = np.ascontiguousarray(np.concatenate(mats))
+        self.nqubits = nq
+        h = P()
+        check(lib().qcw_batch_create(len(circuits), nq.ctypes.data_as(P), begin.ctypes.data_as(P),
+                                     ctypes.cast(descs, P), self.matrices.ctypes.data_as(P), int(fuse_k),
+                                     P(stream), ctypes.byref(h)), "qcw_batch_create")
+        self.h = h
+
+    def run(self):
+        check(lib().qcw_batch_run(self.h), "qcw_batch_run")
+
+    def wait(self, timeout_s: float = -1.0):
+        check(lib().qcw_batch_wait(self.h, float(timeout_s)), "qcw_batch_wait")
+
+    def results(self):
+        """(list of per-circuit p1 arrays, purity array, trace array)."""
+        p1 = np.zeros(int(self.nqubits.sum()), dtype=np.float64)
+        pur = np.zeros(len(self.nqubits), dtype=np.float64)
+        tr = np.zeros(len(self.nqubits), dtype=np.float64)
+        check(lib().qcw_batch_results(self.h, _p(p1), _p(pur), _p(tr)), "qcw_batch_results")
+        out, o = [], 0
+        for n in self.nqubits:
+            out.append(p1[o:o + n].copy())
+            o += n
+        return out, pur, tr
+
+    def get_state(self, j: int) -> np.ndarray:
+        n = int(self.nqubits[j])
+        out = np.empty((1 << n, 1 << n), dtype=np.complex128)
+        check(lib().qcw_batch_get_state(self.h, int(j), _p(out)), "qcw_batch_get_state")
+        return out
+
+    def info(self) -> dict:
+        it, ps, ph = LL(), LL(), LL()
+        md = D()
+        check(lib().qcw_batch_info(self.h, ctypes.byref(it), ctypes.byref(ps), ctypes.byref(ph), ctypes.byref(md)),
+              "qcw_batch_info")
+        return {"items": it.value, "passes": ps.value, "phases": ph.value, "modeled_sm_s": md.value}
+
+    def set_wait_limit(self, polls: int, stall_item: int = -1):
+        check(lib().qcw_batch_set_wait_limit(self.h, int(polls), int(stall_item)), "qcw_batch_set_wait_limit")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().qcw_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """qcw_server_*: continuous batching of circuit requests."""
+
+    def __init__(self, budget_bytes: int, max_live: int = 4096, passes_per_step: int = 4, stream: int = 0):
+        h = P()
+        check(lib().qcw_server_create(int(budget_bytes), int(max_live), int(passes_per_step), P(stream),
+                                      ctypes.byref(h)), "qcw_server_create")
+        self.h = h
+        self._buf = (QcwResult * 256)()
+
+    def submit(self, circuit, packed: "PackedOps | None" = None) -> int:
+        """Queue a workloads.Circuit (optionally with its op list packed in advance)."""
+        p = packed or PackedOps(circuit.ops)
+        rid = LL()
+        check(lib().qcw_server_submit(self.h, int(circuit.n), ctypes.cast(p.descs, P), p.n_ops,
+                                      p.matrices.ctypes.data_as(P), ctypes.byref(rid)), "qcw_server_submit")
+        return rid.value
+
+    def step(self) -> int:
+        k = I()
+        check(lib().qcw_server_step(self.h, ctypes.byref(k)), "qcw_server_step")
+        return k.value
+
+    def drain(self, timeout_s: float = -1.0):
+        check(lib().qcw_server_drain(self.h, float(timeout_s)), "qcw_server_drain")
+
+    def poll(self):
+        """Finished results as dicts (id, n, status, trace, purity, p1, t_submit, t_done)."""
+        out = []
+        while True:
+            c = I()
+            check(lib().qcw_server_poll(self.h, ctypes.cast(self._buf, P), len(self._buf), ctypes.byref(c)),
+                  "qcw_server_poll")
+            for i in range(c.value):
+                r = self._buf[i]
+                out.append({"id": r.id, "n": r.nqubits, "status": r.status, "trace": r.trace, "purity": r.purity,
+                            "p1": np.array(r.p1[:r.nqubits]), "t_submit": r.t_submit, "t_done": r.t_done})
+            if c.value < len(self._buf):
+                return out
+
+    def stats(self) -> dict:
+        w, l, c, b = LL(), LL(), LL(), LL()
+        check(lib().qcw_server_stats(self.h, ctypes.byref(w), ctypes.byref(l), ctypes.byref(c), ctypes.byref(b)),
+              "qcw_server_stats")
+        return {"waiting": w.value, "live": l.value, "completed": c.value, "bytes_in_use": b.value}
+
+    def set_limits(self, wait_limit_s: float, polls: int, stall_next_step: bool = False):
+        check(lib().qcw_server_set_limits(self.h, float(wait_limit_s), int(polls), int(bool(stall_next_step))),
+              "qcw_server_set_limits")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().qcw_server_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

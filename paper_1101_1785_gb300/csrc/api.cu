@@ -456,23 +456,22 @@ extern "C" qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkr
     return submit(ctx, std::move(op));
 }
 
-extern "C" qcw_status qcw_apply_ops(qcw_ctx *ctx, const qcw_op *ops, int nops, const double *matrices)
+qcw_status qcw::convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out)
 {
-    CHECK_CTX(ctx);
     if (nops < 0 || (nops > 0 && (!ops || !matrices))) return set_error(QCW_EINVAL, "bad op list");
     for (int i = 0; i < nops; i++) {  // validate everything first: all or nothing
         const qcw_op &o = ops[i];
         if (o.offset < 0) return set_error(QCW_EINVAL, "negative matrix offset");
         if (o.kind == QCW_OP_GATE) {
             if (o.k < 1 || o.k > QCW_MAX_GATE_QUBITS) return set_error(QCW_EINVAL, "k out of range");
-            qcw_status st = check_qubits(ctx->n, o.qubits, o.k, nullptr, 0);
+            qcw_status st = check_qubits(n, o.qubits, o.k, nullptr, 0);
             if (st) return st;
             if (!all_finite(matrices + o.offset, (size_t)2 << (2 * o.k)))
                 return set_error(QCW_EINVAL, "non-finite matrix entry");
         } else if (o.kind == QCW_OP_KRAUS) {
             if (o.k < 1 || o.k > 2) return set_error(QCW_EINVAL, "channels act on 1 or 2 qubits");
             if (o.nkraus < 1 || o.nkraus > 16) return set_error(QCW_EINVAL, "nkraus out of range");
-            qcw_status st = check_qubits(ctx->n, o.qubits, o.k, nullptr, 0);
+            qcw_status st = check_qubits(n, o.qubits, o.k, nullptr, 0);
             if (st) return st;
             if (!all_finite(matrices + o.offset, ((size_t)2 * o.nkraus) << (2 * o.k)))
                 return set_error(QCW_EINVAL, "non-finite matrix entry");
@@ -480,6 +479,7 @@ extern "C" qcw_status qcw_apply_ops(qcw_ctx *ctx, const qcw_op *ops, int nops, c
             return set_error(QCW_EINVAL, "bad op kind");
         }
     }
+    out.reserve(out.size() + nops);
     for (int i = 0; i < nops; i++) {
         const qcw_op &o = ops[i];
         QOp op;
@@ -492,7 +492,19 @@ extern "C" qcw_status qcw_apply_ops(qcw_ctx *ctx, const qcw_op *ops, int nops, c
         } else {
             op.m = kraus_superop(to_c128(matrices + o.offset, (size_t)o.nkraus << (2 * o.k)), o.nkraus, o.k);
         }
-        qcw_status st = submit(ctx, std::move(op));
+        out.push_back(std::move(op));
+    }
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_apply_ops(qcw_ctx *ctx, const qcw_op *ops, int nops, const double *matrices)
+{
+    CHECK_CTX(ctx);
+    std::vector<QOp> conv;
+    qcw_status st = convert_ops(ctx->n, ops, nops, matrices, conv);
+    if (st) return st;
+    for (QOp &op : conv) {
+        st = submit(ctx, std::move(op));
         if (st) return st;
     }
     return QCW_OK;

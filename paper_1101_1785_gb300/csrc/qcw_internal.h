@@ -127,6 +127,9 @@ qcw_status fused_flush(qcw_ctx *ctx);
 void fused_destroy(qcw_ctx *ctx);
 void fused_collect_timing(qcw_ctx *ctx);
 qcw_status plain_apply(qcw_ctx *c, const QOp &op);
+// Validate an op list against an n-qubit register and convert it to queued operations
+// (Kraus sets become superoperators); nothing is appended on error.
+qcw_status convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out);
 qcw_status set_error(qcw_status st, const std::string &msg);
 qcw_status cuda_error(cudaError_t e, const char *what);
 }  // namespace qcw

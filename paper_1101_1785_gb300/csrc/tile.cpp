@@ -1,0 +1,71 @@
+// Host side of the tile descriptors: tile bit selection and packing of planner output.
+#include "tile.h"
+
+namespace qcw {
+
+size_t tile_smem_bytes(int TB, int L)
+{
+    return ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + 256 * sizeof(float2);
+}
+
+// Tile bits of a pass: rows and columns of Q, then the lowest column bits until tbmax bits
+// (or all column bits are in).
+static void tile_layout(const std::vector<int> &Q, int n, int tbmax, FPass &fp)
+{
+    uint64_t in = 0;
+    for (int q : Q) {
+        in |= 1ull << (n - 1 - q);
+        in |= 1ull << (2 * n - 1 - q);
+    }
+    int want = tbmax < 2 * n ? tbmax : 2 * n;
+    for (int v = 0; v < n && __builtin_popcountll(in) < want; v++) in |= 1ull << v;
+    int tb = 0, ob = 0;
+    for (int v = 0; v < 2 * n; v++) {
+        if (in & (1ull << v)) fp.tbits[tb++] = (int8_t)v;
+        else fp.obits[ob++] = (int8_t)v;
+    }
+    fp.TB = tb;
+    fp.nother = ob;
+    int L = 0;
+    while (L < tb && fp.tbits[L] == L) L++;
+    fp.L = L;
+}
+
+static int tile_pos(const FPass &fp, int vbit)
+{
+    for (int j = 0; j < fp.TB; j++)
+        if (fp.tbits[j] == vbit) return j;
+    return -1;
+}
+
+void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TilePlan &out)
+{
+    for (const PassPlan &pp : plan) {
+        FPass fp{};
+        tile_layout(pp.Q, n, tbmax, fp);
+        fp.nphase = (int)pp.phases.size();
+        fp.phase0 = (int)out.phases.size();
+        for (const PhasePlan &ph : pp.phases) {
+            FPhase f{};
+            f.nq = ph.nq;
+            f.coef = (int)out.coefs.size();
+            if (ph.nq == 2) {
+                f.pos[0] = (int8_t)tile_pos(fp, 2 * n - 1 - ph.qa);
+                f.pos[1] = (int8_t)tile_pos(fp, 2 * n - 1 - ph.qb);
+                f.pos[2] = (int8_t)tile_pos(fp, n - 1 - ph.qa);
+                f.pos[3] = (int8_t)tile_pos(fp, n - 1 - ph.qb);
+                out.nphase2++;
+            } else {
+                f.pos[0] = (int8_t)tile_pos(fp, 2 * n - 1 - ph.qa);
+                f.pos[1] = (int8_t)tile_pos(fp, n - 1 - ph.qa);
+                out.nphase1++;
+            }
+            for (const c128 &z : ph.S) out.coefs.push_back(make_float2((float)z.real(), (float)z.imag()));
+            out.phases.push_back(f);
+        }
+        out.passes.push_back(fp);
+        out.smem.push_back(tile_smem_bytes(fp.TB, fp.L));
+    }
+}
+
+}  // namespace qcw

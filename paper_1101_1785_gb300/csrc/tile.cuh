@@ -1,0 +1,210 @@
+// Device side of a fused pass over one tile: cp.async load into shared memory, the pass's
+// phases applied in place, write-back.  Used by k_fused_pass (one tile per CTA) and by the
+// batched persistent kernel (a CTA walks all tiles of all passes of one circuit).
+//
+// A phase is a composed superoperator on one or two qubits of the pass.  A two-qubit phase
+// gathers 16-element groups (the row quartet x column quartet of Sec. 3.2 for the phase's
+// qubits), a one-qubit phase 4-element groups (row pair x column pair, Sec. 3.1); each
+// group is multiplied by the phase superoperator and scattered back.  Groups of one phase
+// are disjoint, so no atomics are needed.
+#pragma once
+#include "qcw_device.cuh"
+#include "tile.h"
+
+namespace qcw {
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ unsigned ins0u(unsigned x, int p)
+{
+    unsigned lo = x & ((1u << p) - 1u);
+    return ((x ^ lo) << 1) | lo;
+}
+
+// Two-qubit phase: 16x16 superoperator S (shared memory, row-major) on every group.
+// G groups per thread share each coefficient load.
+template <int G>
+__device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
+                                            const float2 *__restrict__ S)
+{
+    const unsigned d0 = 1u << F.pos[0], d1 = 1u << F.pos[1], d2 = 1u << F.pos[2], d3 = 1u << F.pos[3];
+    int p[4] = {F.pos[0], F.pos[1], F.pos[2], F.pos[3]};
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = a + 1; b < 4; b++)
+            if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
+    const unsigned ng = 1u << (TB - 4);
+    const float4 *S4 = reinterpret_cast<const float4 *>(S);
+    for (unsigned g0 = threadIdx.x; g0 < ng; g0 += G * kTileThreads) {
+        unsigned base[G];
+        float2 x[G][16];
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            unsigned g = g0 + j * kTileThreads;
+            base[j] = ins0u(ins0u(ins0u(ins0u(g, p[0]), p[1]), p[2]), p[3]);
+#pragma unroll
+            for (int e = 0; e < 16; e++)
+                x[j][e] = tile[base[j] + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) +
+                               ((e & 1) ? d3 : 0u)];
+        }
+        // The member loop stays rolled so that the 256 coefficients are re-read from shared
+        // memory (broadcast) instead of being hoisted into registers.
+#pragma unroll 1
+        for (int e = 0; e < 16; e++) {
+            const unsigned oe = ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u);
+            float2 y[G];
+#pragma unroll
+            for (int j = 0; j < G; j++) y[j] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int f = 0; f < 16; f += 2) {
+                float4 c = S4[8 * e + (f >> 1)];
+                float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
+#pragma unroll
+                for (int j = 0; j < G; j++) {
+                    cfma(y[j], c0, x[j][f]);
+                    cfma(y[j], c1, x[j][f + 1]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < G; j++) tile[base[j] + oe] = y[j];
+        }
+    }
+}
+
+// One-qubit phase: 4x4 superoperator on every (row pair x column pair) group.
+__device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, const FPhase &F,
+                                            const float2 *__restrict__ S)
+{
+    const int pr = F.pos[0], pc = F.pos[1];
+    const int lo = pr < pc ? pr : pc, hi = pr < pc ? pc : pr;
+    const unsigned dr = 1u << pr, dc = 1u << pc;
+    float2 s[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) s[i] = S[i];
+    const unsigned ng = 1u << (TB - 2);
+    for (unsigned g = threadIdx.x; g < ng; g += kTileThreads) {
+        unsigned b = ins0u(ins0u(g, lo), hi);
+        float2 x[4] = {tile[b], tile[b + dc], tile[b + dr], tile[b + dr + dc]};
+        float2 y[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            y[e] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int f = 0; f < 4; f++) cfma(y[e], s[4 * e + f], x[f]);
+        }
+        tile[b] = y[0];
+        tile[b + dc] = y[1];
+        tile[b + dr] = y[2];
+        tile[b + dr + dc] = y[3];
+    }
+}
+
+// Shared-memory carve-up for a pass: tile | high-offset table | one superoperator.
+struct TileSmem {
+    float2 *tile;
+    uint64_t *hoff;
+    float2 *S;
+};
+
+__device__ __forceinline__ TileSmem tile_smem(unsigned char *smem, int TB, int L)
+{
+    TileSmem t;
+    t.tile = reinterpret_cast<float2 *>(smem);
+    t.hoff = reinterpret_cast<uint64_t *>(t.tile + (1u << TB));
+    t.S = reinterpret_cast<float2 *>(t.hoff + ((1u << (TB - L)) | 1u) + 1u);  // 16-byte aligned
+    return t;
+}
+
+// Offsets (relative to the tile base) of the 2^(TB-L) contiguous runs of a tile.
+__device__ __forceinline__ void tile_hoff(const FPass &P, uint64_t *hoff)
+{
+    const int TB = P.TB, L = P.L;
+    for (unsigned i = threadIdx.x; i < (1u << (TB - L)); i += kTileThreads) {
+        uint64_t o = 0;
+        for (int j = 0; j < TB - L; j++) o |= (uint64_t)((i >> j) & 1u) << P.tbits[L + j];
+        hoff[i] = o;
+    }
+}
+
+__device__ __forceinline__ uint64_t tile_base(const FPass &P, uint64_t tile)
+{
+    uint64_t base = 0;
+    for (int j = 0; j < P.nother; j++) base |= ((tile >> j) & 1ull) << P.obits[j];
+    return base;
+}
+
+// Bring tile `t` of pass P into shared memory (or, with init, write |0..0><0..0| there: the
+// element of global index 0 is tile index 0 of tile 0).  Expects sm.hoff filled for P.
+__device__ __forceinline__ void tile_load(const float2 *__restrict__ rho, const FPass &P, uint64_t t, const TileSmem &sm,
+                                          bool init)
+{
+    const int TB = P.TB, L = P.L;
+    const unsigned nvec = 1u << (TB - 1);
+    if (init) {
+        float4 *t4 = reinterpret_cast<float4 *>(sm.tile);
+        for (unsigned v = threadIdx.x; v < nvec; v += kTileThreads)
+            t4[v] = (t == 0 && v == 0) ? make_float4(1.f, 0.f, 0.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        const uint64_t base = tile_base(P, t);
+        const unsigned lmask = (1u << L) - 1u;
+        for (unsigned v = threadIdx.x; v < nvec; v += kTileThreads) {
+            unsigned e = 2 * v;
+            cp_async16(&sm.tile[e], rho + base + sm.hoff[e >> L] + (e & lmask));
+        }
+        cp_async_wait_all();
+    }
+    __syncthreads();
+}
+
+// Apply the phases of pass P to the tile in shared memory.
+__device__ __forceinline__ void tile_phases(const FPass &P, const FPhase *__restrict__ phases,
+                                            const float2 *__restrict__ coefs, const TileSmem &sm)
+{
+    const int TB = P.TB;
+    for (int ph = 0; ph < P.nphase; ph++) {
+        const FPhase F = phases[P.phase0 + ph];
+        const int ncoef = F.nq == 2 ? 256 : 16;
+        for (int i = threadIdx.x; i < ncoef; i += kTileThreads) sm.S[i] = coefs[F.coef + i];
+        __syncthreads();
+        if (F.nq == 2) {
+            if (TB >= 13) tile_phase2<2>(sm.tile, TB, F, sm.S);
+            else tile_phase2<1>(sm.tile, TB, F, sm.S);
+        } else {
+            tile_phase1(sm.tile, TB, F, sm.S);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void tile_store(float2 *__restrict__ rho, const FPass &P, uint64_t t, const TileSmem &sm)
+{
+    const int TB = P.TB, L = P.L;
+    const uint64_t base = tile_base(P, t);
+    const unsigned nvec = 1u << (TB - 1);
+    const unsigned lmask = (1u << L) - 1u;
+    const float4 *t4 = reinterpret_cast<const float4 *>(sm.tile);
+    for (unsigned v = threadIdx.x; v < nvec; v += kTileThreads) {
+        unsigned e = 2 * v;
+        *reinterpret_cast<float4 *>(rho + base + sm.hoff[e >> L] + (e & lmask)) = t4[v];
+    }
+}
+
+// Load tile `t` of pass P, apply its phases, store it.  Expects sm.hoff filled for P and a
+// __syncthreads() after that; the caller synchronises before reusing shared memory.
+__device__ __forceinline__ void tile_process(float2 *__restrict__ rho, const FPass &P, uint64_t t,
+                                             const FPhase *__restrict__ phases, const float2 *__restrict__ coefs,
+                                             const TileSmem &sm, bool init = false)
+{
+    tile_load(rho, P, t, sm, init);
+    tile_phases(P, phases, coefs, sm);
+    tile_store(rho, P, t, sm);
+}
+
+}  // namespace qcw

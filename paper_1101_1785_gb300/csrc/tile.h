@@ -1,0 +1,52 @@
+// Pass / phase descriptors shared by the fused-pass kernel and the batched persistent
+// kernel, and the host routine that turns planner output into them.
+//
+// A pass touches a qubit set Q.  Its tile is the set of 2^TB elements whose flat indices
+// differ only in the "tile bits": the row and column bits of Q plus the lowest column bits
+// (contiguous runs of 2^L elements).  The other 2n - TB bits enumerate the tiles.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "planner.h"
+
+namespace qcw {
+
+struct FPass {
+    int TB;            // tile bits
+    int L;             // tile bits 0..L-1 are virtual bits 0..L-1 (contiguous run)
+    int nother;        // 2n - TB
+    int nphase;
+    int phase0;        // first phase in the phase array
+    int pad;
+    int8_t tbits[16];  // virtual bit of tile bit j (ascending)
+    int8_t obits[40];  // virtual bits outside the tile (ascending)
+};
+
+struct FPhase {
+    int nq;            // 1 or 2
+    int coef;          // offset of the superoperator in the coefficient array (float2 units)
+    int8_t pos[4];     // tile positions of (r_a, r_b, c_a, c_b); (r_a, c_a) when nq == 1
+    int pad;
+};
+
+constexpr int kTileThreads = 256;  // threads per CTA of the tile kernels
+constexpr int kTileBitsMax = 14;   // largest tile: 2^14 complex64 = 128 KiB
+
+// Host-side descriptor arrays for a list of passes.
+struct TilePlan {
+    std::vector<FPass> passes;
+    std::vector<FPhase> phases;
+    std::vector<float2> coefs;
+    std::vector<size_t> smem;  // dynamic shared memory per pass
+    int nphase2 = 0, nphase1 = 0;
+};
+
+// Append the passes of `plan` (an n-qubit register, tiles of at most tbmax bits) to `out`.
+void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TilePlan &out);
+
+// Dynamic shared memory of a tile kernel for a pass with TB tile bits and an L-bit run.
+size_t tile_smem_bytes(int TB, int L);
+
+}  // namespace qcw
