@@ -46,6 +46,11 @@ def parse_args():
     ap.add_argument("--impl", default="qcw", choices=["qcw", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-gates", type=int, default=1, help="gates of the oracle sample")
+    ap.add_argument("--workload", default="circuit14", choices=["circuit14", "batch", "serve"],
+                    help="circuit14: the 14-qubit benchmark (default); batch: 512 circuits of 4..10 qubits in "
+                         "one launch; serve: Poisson request stream through the continuous-batching server")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--qubits", type=int, default=N_QUBITS,
                     help="register size (14 is the benchmark; smaller sizes are for profiling)")
     return ap.parse_args()
@@ -336,10 +341,155 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- batch / serve
+def _loop_one_at_a_time(q, circuits, packed, reps=1):
+    """The plain GPU path: one context per size, each circuit run and read out on its own."""
+    import numpy as np
+
+    dens = {}
+    for c in circuits:
+        if c.n not in dens:
+            dens[c.n] = q.Density(c.n)
+            dens[c.n].set_mode(q.QCW_MODE_FUSED, 0)
+    out = np.zeros(len(circuits))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for j, (c, p) in enumerate(zip(circuits, packed)):
+            d = dens[c.n]
+            d.reset()
+            d.apply_packed(p)
+            d.probabilities()
+            out[j] = d.purity()
+    dt = (time.perf_counter() - t0) / reps
+    for d in dens.values():
+        d.close()
+    return dt, out
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import workloads as wl
+
+    __graft_entry__.build()
+    import paper_1101_1785_gb300 as q
+
+    torch.cuda.init()
+    circuits = wl.config4_batch()
+    gates = sum(c.n_gates for c in circuits)
+    t0 = time.perf_counter()
+    b = q.Batch(circuits)
+    t_create = time.perf_counter() - t0
+    for _ in range(max(3, args.warmup)):
+        b.run()
+        b.wait()
+    sampler = ClockSampler(0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.run()
+        b.wait()
+    dt = (time.perf_counter() - t0) / args.steps
+    clocks = sampler.stop()
+    _, pur, _ = b.results()
+    info = b.info()
+    b.close()
+    packed = [q.PackedOps(c.ops) for c in circuits]
+    _loop_one_at_a_time(q, circuits[:16], packed[:16])  # warm-up
+    dt_loop, pur_loop = _loop_one_at_a_time(q, circuits, packed)
+    print(json.dumps({
+        "metric": "gate-applications/s, 512-circuit batch (n ~ U{4..10}, depth ~ U{50..400}, AD+PD)",
+        "value": gates / dt, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "512 seeded circuits, one persistent graph-captured launch", "circuits": len(circuits),
+                   "gates": gates},
+        "circuits_per_s": len(circuits) / dt,
+        "plain_loop": {"value": gates / dt_loop, "ms_per_batch": dt_loop * 1e3,
+                       "circuits_per_s": len(circuits) / dt_loop},
+        "speedup_vs_plain_loop": dt_loop / dt,
+        "max_abs_purity_diff_vs_plain": float(np.abs(pur - pur_loop).max()),
+        "plan": info, "create_s": t_create, "clocks": clocks,
+    }), flush=True)
+
+
+def run_serve(args):
+    import threading
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import workloads as wl
+
+    __graft_entry__.build()
+    import paper_1101_1785_gb300 as q
+
+    torch.cuda.init()
+    reqs = wl.config5_requests(rate=args.rate, duration=args.duration)
+    warm = wl.config5_requests(rate=args.rate, duration=0.2, index=1)
+    packed = [q.PackedOps(c.ops) for _, c in reqs]
+    wpacked = [q.PackedOps(c.ops) for _, c in warm]
+    srv = q.Server(48 << 30, max_live=8192, passes_per_step=4)
+    for (_, c), p in zip(warm, wpacked):
+        srv.submit(c, p)
+    srv.drain(120.0)
+    srv.poll()
+
+    start = time.monotonic() + 0.05
+    arrivals = [start + t for t, _ in reqs]
+    ids = {}
+    done_sub = threading.Event()
+
+    def dispatcher():
+        for i, ((_, c), p) in enumerate(zip(reqs, packed)):
+            wait = arrivals[i] - time.monotonic()
+            if wait > 0:
+                time.sleep(wait)
+            ids[srv.submit(c, p)] = i
+        done_sub.set()
+
+    th = threading.Thread(target=dispatcher, daemon=True)
+    sampler = ClockSampler(0)
+    th.start()
+    results = []
+    while not (done_sub.is_set() and len(results) == len(reqs)):
+        srv.step()
+        results += srv.poll()
+        if not results and time.monotonic() - start > args.duration + 600:
+            break
+    th.join()
+    clocks = sampler.stop()
+    srv.close()
+    lat = np.array([r["t_done"] - arrivals[ids[r["id"]]] for r in results])
+    t_end = max(r["t_done"] for r in results)
+    bad = sum(1 for r in results if r["status"] != 0 or abs(r["trace"] - 1) > 1e-5)
+    gates = sum(c.n_gates for _, c in reqs)
+    sample = min(len(reqs), 2000)
+    dt_loop, _ = _loop_one_at_a_time(q, [c for _, c in reqs[:sample]], packed[:sample])
+    print(json.dumps({
+        "metric": "req/s and p99 latency, Poisson request stream (n 3..13, depth 20..500, mixed noise)",
+        "value": len(results) / (t_end - start), "unit": "req/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "c64", "data": "synthetic",
+        "config": {"workload": f"Poisson {args.rate:g} req/s for {args.duration:g} s, budget 48 GiB (16*4^n per "
+                               f"request), 4 passes per engine step", "requests": len(reqs)},
+        "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                       "max": float(lat.max() * 1e3)},
+        "gate_apps_per_s": gates / (t_end - start), "offered_req_per_s": args.rate,
+        "bad_results": bad,
+        "plain_loop": {"req_per_s": sample / dt_loop, "sample": sample},
+        "clocks": clocks,
+    }), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -208,7 +208,7 @@ QCW_API qcw_status qcw_partial_trace_static(const void *dev_rho, int nqubits, co
  * qcw_apply_ops).  fuse_k (0 = chosen per circuit by the cost model, else 2..5) bounds the
  * qubits of a fused pass.  Creation plans every circuit, allocates one device arena for all
  * states and captures the whole run (one persistent kernel) in a CUDA graph on cuda_stream
- * (NULL = legacy default stream).  All arrays are copied; the caller may free them on return. */
+ * (NULL: a non-blocking stream owned by the batch, since the legacy stream cannot be captured).  All arrays are copied; the caller may free them on return. */
 typedef struct qcw_batch qcw_batch;
 QCW_API qcw_status qcw_batch_create(int ncirc, const int *nqubits, const long long *op_begin, const qcw_op *ops,
                                     const double *matrices, int fuse_k, void *cuda_stream, qcw_batch **out);
@@ -253,6 +253,7 @@ typedef struct {
     double p1[QCW_MAX_QUBITS]; /* P(q = 1) for q < nqubits */
     double t_submit, t_done;   /* host steady-clock seconds */
 } qcw_result;
+/* cuda_stream NULL: the server creates and owns a non-blocking stream. */
 QCW_API qcw_status qcw_server_create(size_t budget_bytes, int max_live, int passes_per_step, void *cuda_stream,
                                      qcw_server **out);
 /* Plan and queue one request; *id receives its id.  Thread-safe with respect to qcw_server_step. */

@@ -20,6 +20,7 @@ using namespace qcw;
 struct qcw_batch {
     int dev = 0;
     cudaStream_t stream = nullptr;
+    bool owns_stream = false;
     std::vector<Program> progs;
     std::vector<size_t> rho_off;
     std::vector<int> red_first, red_n;
@@ -66,6 +67,7 @@ static void batch_free(qcw_batch *b)
     cudaFree(b->dred);
     if (b->hred) cudaFreeHost(b->hred);
     if (b->herr) cudaFreeHost(b->herr);
+    if (b->owns_stream) cudaStreamDestroy(b->stream);
     delete b;
 }
 
@@ -110,6 +112,14 @@ extern "C" qcw_status qcw_batch_create(int ncirc, const int *nqubits, const long
     }
     qcw_batch *b = new qcw_batch();
     b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!b->stream) {  // the legacy default stream cannot be captured: use a stream of our own
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return set_error(QCW_ECUDA, "batch stream");
+        }
+        b->owns_stream = true;
+    }
     qcw_status st = QCW_OK;
     const int tbmax = 13;
     // plan every circuit (ops are validated against its own register size)

@@ -187,7 +187,7 @@ int choose_fuse_k(const std::vector<QOp> &ops, size_t b, size_t e, int n, int tb
     double bc = -1;
     for (int k = 2; k <= 5 && k <= n; k++) {
         TilePlan tp;
-        append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp);
+        append_tile_plan(plan_passes(ops, b, e, n, k, true), n, tbmax, tp);
         double c = model_cost(tp, n);
         if (bc < 0 || c < bc) {
             bc = c;

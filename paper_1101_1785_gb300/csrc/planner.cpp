@@ -14,60 +14,124 @@
 
 namespace qcw {
 
-std::vector<c128> unitary_superop(const std::vector<c128> &u, int k)
+// Native superoperator of an op (4x4 for one qubit, 16x16 for two), index (R, C) with the
+// op's qubits in its own order; unitaries become U (x) conj(U).
+static void op_superop(const QOp &op, c128 *out)
 {
-    int d = 1 << k, D = d * d;
-    std::vector<c128> s((size_t)D * D);
+    if (op.kind != 0) {
+        for (size_t i = 0; i < op.m.size(); i++) out[i] = op.m[i];
+        return;
+    }
+    const int d = 1 << op.k, D = d * d;
+    const c128 *u = op.m.data();
     for (int r2 = 0; r2 < d; r2++)
         for (int c2 = 0; c2 < d; c2++)
             for (int r = 0; r < d; r++)
-                for (int c = 0; c < d; c++)
-                    s[(size_t)(r2 * d + c2) * D + (r * d + c)] = u[r2 * d + r] * std::conj(u[c2 * d + c]);
-    return s;
+                for (int c = 0; c < d; c++) out[(r2 * d + c2) * D + (r * d + c)] = u[r2 * d + r] * std::conj(u[c2 * d + c]);
 }
 
-// S_phase <- S_op (lifted to the phase qubits) * S_phase.
-// Phase bits of an index e: for nq == 2, r_a = bit 3, r_b = bit 2, c_a = bit 1, c_b = bit 0;
-// for nq == 1, r_a = bit 1, c_a = bit 0.
-static void fold_op(PhasePlan &ph, const QOp &op)
-{
-    const int nq = ph.nq, D = 1 << (2 * nq);
-    const int k = op.k, dk = 1 << k, Dk = dk * dk;
-    const std::vector<c128> sop = op.kind == 0 ? unitary_superop(op.m, k) : op.m;
-    // slot of each op qubit in the phase (0 = a, 1 = b)
-    int slot[2];
-    for (int j = 0; j < k; j++) slot[j] = op.qubits[j] == ph.qa ? 0 : 1;
-    auto rbit = [&](int e, int s) { return nq == 2 ? (e >> (3 - s)) & 1 : (e >> 1) & 1; };
-    auto cbit = [&](int e, int s) { return nq == 2 ? (e >> (1 - s)) & 1 : e & 1; };
-    // projection of a phase index onto the op's local index, and the mask of "other" bits
-    auto op_index = [&](int e) {
-        int R = 0, C = 0;
-        for (int j = 0; j < k; j++) {
-            R |= rbit(e, slot[j]) << (k - 1 - j);
-            C |= cbit(e, slot[j]) << (k - 1 - j);
-        }
-        return R * dk + C;
-    };
-    int opmask = 0;  // phase-index bits that belong to the op
-    for (int j = 0; j < k; j++) {
-        if (nq == 2) opmask |= (1 << (3 - slot[j])) | (1 << (1 - slot[j]));
-        else opmask |= 3;
+// Phase accumulator: S (D x D, D = 4^nq) kept as split real / imaginary rows so that
+// S <- A S is a set of length-D row AXPYs that the compiler vectorises.  Runs of consecutive
+// ops on the same qubit list are first multiplied at their native size and lifted once.
+struct PhaseAcc {
+    int nq = 0, qa = -1, qb = -1, D = 0;
+    double Sr[256], Si[256];
+    // pending run
+    int rk = 0, rq[2] = {-1, -1};
+    c128 run[256];
+    bool has_run = false;
+
+    void start(int nq_, int a, int b)
+    {
+        nq = nq_;
+        qa = a;
+        qb = b;
+        D = 1 << (2 * nq);
+        for (int i = 0; i < D * D; i++) Sr[i] = Si[i] = 0;
+        for (int i = 0; i < D; i++) Sr[i * D + i] = 1.0;
+        has_run = false;
     }
-    std::vector<c128> out((size_t)D * D, c128(0, 0));
-    for (int e2 = 0; e2 < D; e2++) {
-        int o2 = op_index(e2);
-        for (int e1 = 0; e1 < D; e1++) {
-            if ((e1 & ~opmask) != (e2 & ~opmask)) continue;
-            c128 w = sop[(size_t)o2 * Dk + op_index(e1)];
-            if (w == c128(0, 0)) continue;
-            const c128 *src = &ph.S[(size_t)e1 * D];
-            c128 *dst = &out[(size_t)e2 * D];
-            for (int e0 = 0; e0 < D; e0++) dst[e0] += w * src[e0];
+
+    // S <- lift(A) * S for a native superoperator A on qubits q[0..k-1].
+    void lift(const c128 *A, int k, const int *q)
+    {
+        const int dk = 1 << k, Dk = dk * dk;
+        int slot[2] = {0, 0};
+        for (int j = 0; j < k; j++) slot[j] = q[j] == qa ? 0 : 1;
+        // phase index bits: nq == 2: r_a = 3, r_b = 2, c_a = 1, c_b = 0; nq == 1: r = 1, c = 0
+        auto rbitpos = [&](int s) { return nq == 2 ? 3 - s : 1; };
+        auto cbitpos = [&](int s) { return nq == 2 ? 1 - s : 0; };
+        int opmask = 0;
+        for (int j = 0; j < k; j++) opmask |= (1 << rbitpos(slot[j])) | (1 << cbitpos(slot[j]));
+        int oi[16];  // op-local index of every phase index
+        for (int e = 0; e < D; e++) {
+            int R = 0, C = 0;
+            for (int j = 0; j < k; j++) {
+                R |= ((e >> rbitpos(slot[j])) & 1) << (k - 1 - j);
+                C |= ((e >> cbitpos(slot[j])) & 1) << (k - 1 - j);
+            }
+            oi[e] = R * dk + C;
+        }
+        double Nr[256], Ni[256];
+        for (int e2 = 0; e2 < D; e2++) {
+            double *nr = Nr + e2 * D, *ni = Ni + e2 * D;
+            for (int c = 0; c < D; c++) nr[c] = ni[c] = 0;
+            for (int e1 = 0; e1 < D; e1++) {
+                if ((e1 & ~opmask) != (e2 & ~opmask)) continue;
+                const c128 w = A[oi[e2] * Dk + oi[e1]];
+                const double wr = w.real(), wi = w.imag();
+                if (wr == 0 && wi == 0) continue;
+                const double *sr = Sr + e1 * D, *si = Si + e1 * D;
+                for (int c = 0; c < D; c++) {
+                    nr[c] += wr * sr[c] - wi * si[c];
+                    ni[c] += wr * si[c] + wi * sr[c];
+                }
+            }
+        }
+        for (int i = 0; i < D * D; i++) {
+            Sr[i] = Nr[i];
+            Si[i] = Ni[i];
         }
     }
-    ph.S.swap(out);
-    ph.nops++;
-}
+
+    void flush()
+    {
+        if (has_run) lift(run, rk, rq);
+        has_run = false;
+    }
+
+    void add(const QOp &op)
+    {
+        c128 A[256];
+        op_superop(op, A);
+        const bool same = has_run && rk == op.k && rq[0] == op.qubits[0] && (op.k == 1 || rq[1] == op.qubits[1]);
+        if (same) {  // run <- A * run at native size
+            const int Dk = 1 << (2 * op.k);
+            c128 T[256];
+            for (int i = 0; i < Dk; i++)
+                for (int j = 0; j < Dk; j++) {
+                    c128 acc = 0;
+                    for (int l = 0; l < Dk; l++) acc += A[i * Dk + l] * run[l * Dk + j];
+                    T[i * Dk + j] = acc;
+                }
+            for (int i = 0; i < Dk * Dk; i++) run[i] = T[i];
+            return;
+        }
+        flush();
+        rk = op.k;
+        rq[0] = op.qubits[0];
+        rq[1] = op.k > 1 ? op.qubits[1] : -1;
+        for (int i = 0; i < (1 << (4 * op.k)); i++) run[i] = A[i];
+        has_run = true;
+    }
+
+    void result(std::vector<c128> &out)
+    {
+        flush();
+        out.resize((size_t)D * D);
+        for (int i = 0; i < D * D; i++) out[i] = c128(Sr[i], Si[i]);
+    }
+};
 
 static void identity(std::vector<c128> &s, int D)
 {
@@ -84,8 +148,10 @@ static unsigned qmask(const QOp &op)
 
 static int popc(unsigned x) { return __builtin_popcount(x); }
 
-std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, size_t end, int n, int kmax)
+std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, size_t end, int n, int kmax,
+                                  bool count_only)
 {
+    PhaseAcc acc;
     std::vector<PassPlan> passes;
     std::vector<size_t> rem;
     for (size_t i = begin; i < end; i++) rem.push_back(i);
@@ -141,9 +207,14 @@ std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, siz
                     if (ph.qa < 0) ph.qa = q;
                     else ph.qb = q;
                 }
-            ph.nops = 0;
-            identity(ph.S, 1 << (2 * ph.nq));
-            for (size_t i : pch) fold_op(ph, ops[i]);
+            ph.nops = (int)pch.size();
+            if (!count_only) {
+                acc.start(ph.nq, ph.qa, ph.qb);
+                for (size_t i : pch) acc.add(ops[i]);
+                acc.result(ph.S);
+            } else {
+                identity(ph.S, 0);
+            }
             pp.phases.push_back(std::move(ph));
             prem.swap(prest);
         }

@@ -22,10 +22,9 @@ struct PassPlan {
     int nops;
 };
 
-// Superoperator of a unitary on k qubits: S[(r',c'), (r,c)] = U[r', r] conj(U[c', c]).
-std::vector<c128> unitary_superop(const std::vector<c128> &u, int k);
-
-// Plan ops[begin, end) (all with k <= 2 and no controls) for an n-qubit register.
-std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, size_t end, int n, int kmax);
+// Plan ops[begin, end) (all with k <= 2 and no controls) for an n-qubit register.  With
+// count_only the pass / phase structure is produced without composing the superoperators.
+std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, size_t end, int n, int kmax,
+                                  bool count_only = false);
 
 }  // namespace qcw

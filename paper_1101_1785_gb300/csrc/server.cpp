@@ -102,6 +102,7 @@ struct qcw_server {
     int dev = 0, grid = 0;
     size_t smem = 0;
     cudaStream_t stream = nullptr;
+    bool owns_stream = false;
     size_t budget = 0, used = 0;
     int max_live = 0, passes_per_step = 4;
     long long spin_limit = 20000000;
@@ -144,6 +145,7 @@ static void server_free(qcw_server *s)
     if (s->hred) cudaFreeHost(s->hred);
     if (s->hitems) cudaFreeHost(s->hitems);
     if (s->hint) cudaFreeHost(s->hint);
+    if (s->owns_stream) cudaStreamDestroy(s->stream);
     delete s;
 }
 
@@ -155,6 +157,14 @@ extern "C" qcw_status qcw_server_create(size_t budget_bytes, int max_live, int p
     if (budget_bytes < 4096 || max_live < 1 || passes_per_step < 1) return set_error(QCW_EINVAL, "bad server limits");
     qcw_server *s = new qcw_server();
     s->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!s->stream) {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return set_error(QCW_ECUDA, "server stream");
+        }
+        s->owns_stream = true;
+    }
     s->budget = budget_bytes;
     s->max_live = max_live;
     s->passes_per_step = passes_per_step;
