@@ -2,6 +2,8 @@
 // operation) path and the FP64 readouts.  The fused path lives in fused.cu / planner.cpp.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "qcw_internal.h"
@@ -20,6 +22,22 @@ qcw_status qcw::cuda_error(cudaError_t e, const char *what)
 {
     g_err = std::string(what) + ": " + cudaGetErrorString(e);
     return QCW_ECUDA;
+}
+
+qcw_status qcw::ensure_smem_attr(const void *func, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = set[{func, dev}];
+    if (bytes <= cur) return QCW_OK;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_error(e, "max dynamic shared memory attribute");
+    cur = bytes;
+    return QCW_OK;
 }
 
 #define CK(call)                                                   \

@@ -151,10 +151,10 @@ void engine_launch(const EngineLaunch &L, int grid, size_t smem, cudaStream_t s)
 
 qcw_status engine_prepare(int dev, size_t smem, int *grid)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "engine smem attribute");
+    qcw_status st = ensure_smem_attr(reinterpret_cast<const void *>(k_engine), smem);
+    if (st) return st;
     int occ = 0, nsm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_engine, kTileThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_engine, kTileThreads, smem);
     if (e != cudaSuccess) return cuda_error(e, "engine occupancy");
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_error(e, "SM count");

@@ -50,8 +50,6 @@ struct FusedRuntime {
     std::vector<CachedPlan> cache;
     long long tick = 0;
     std::vector<cudaEvent_t> ev_free, ev_pending;  // pairs: start, stop
-    int smem_set_dev = -1;
-    size_t smem_set_bytes = 0;
 };
 
 static uint64_t fnv(uint64_t h, const void *p, size_t n)
@@ -172,12 +170,8 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
 
     size_t maxsm = 0;
     for (size_t s : hit->smem) maxsm = s > maxsm ? s : maxsm;
-    if (rt->smem_set_dev != c->dev || rt->smem_set_bytes < maxsm) {
-        cudaError_t er = cudaFuncSetAttribute(k_fused_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);
-        if (er != cudaSuccess) return cuda_error(er, "fused smem attribute");
-        rt->smem_set_dev = c->dev;
-        rt->smem_set_bytes = maxsm;
-    }
+    qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
+    if (sst) return sst;
     const FPass *dp = reinterpret_cast<const FPass *>(hit->dbuf);
     const FPhase *dph = reinterpret_cast<const FPhase *>(hit->dbuf + hit->phase_off);
     const float2 *dco = reinterpret_cast<const float2 *>(hit->dbuf + hit->coef_off);

@@ -131,5 +131,8 @@ qcw_status plain_apply(qcw_ctx *c, const QOp &op);
 // (Kraus sets become superoperators); nothing is appended on error.
 qcw_status convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out);
 qcw_status set_error(qcw_status st, const std::string &msg);
+// Raise a kernel's max dynamic shared memory on the current device to at least `bytes`.  The
+// attribute is process-wide per function and device, so it only ever grows.
+qcw_status ensure_smem_attr(const void *func, size_t bytes);
 qcw_status cuda_error(cudaError_t e, const char *what);
 }  // namespace qcw

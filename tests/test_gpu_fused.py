@@ -172,3 +172,19 @@ def test_full_size_n14_config3_prefix(q):
     assert np.abs(got - want).max() <= ATOL
     assert abs(d.trace() - 1) <= TRACE_TOL
     d.close()
+
+
+def test_contexts_of_different_sizes_interleave(q):
+    """Kernel attributes are per process: a small context must not break a big one."""
+    big = wl.random_circuit(10, 30, 21, "mixed", "adpd")
+    small = wl.random_circuit(3, 30, 22, "mixed", "adpd")
+    db, ds = q.Density(10), q.Density(3)
+    db.set_mode(q.QCW_MODE_FUSED, 5)
+    ds.set_mode(q.QCW_MODE_FUSED, 0)
+    for c, d in ((big, db), (small, ds), (big, db), (small, ds)):
+        d.reset()
+        for op in c.ops:
+            d.apply_op(op)
+        assert np.abs(d.get_state() - oracle.run_circuit(c)).max() <= ATOL
+    db.close()
+    ds.close()
