@@ -107,7 +107,7 @@ __device__ void run_whole(const WItem &W, unsigned char *smem, RedShared &sh)
     tile_store(W.rho, P0, 0, sm);
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_engine(EngineLaunch L)
+__global__ void __launch_bounds__(kTileThreads, 2) k_engine(EngineLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
@@ -177,7 +177,8 @@ double model_cost(const TilePlan &tp, int n)
     double el = (double)(1ull << (2 * n));
     double c = 0;
     for (const FPass &p : tp.passes) c += kCostPass * el;
-    for (const FPhase &f : tp.phases) c += (f.nq == 2 ? kCostPhase2 : kCostPhase1) * el;
+    for (const FPhase &f : tp.phases)
+        c += (f.nq == PH_TWO ? kCostPhase2 : f.nq == PH_PRODUCT ? 2 * kCostPhase1 : kCostPhase1) * el;
     return c;
 }
 

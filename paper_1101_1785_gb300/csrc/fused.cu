@@ -10,6 +10,7 @@
 // quartet x column quartet of Sec. 3.2 for the two phase qubits) or 4-element groups (the
 // pair x pair of Sec. 3.1) from shared memory, multiplies them by the phase superoperator
 // and scatters them back.  Groups of one phase are disjoint, so phases need no atomics.
+#include <algorithm>
 #include <cstring>
 
 #include "planner.h"
@@ -21,7 +22,7 @@ namespace qcw {
 constexpr int FT = kTileThreads;
 
 // One CTA per tile of one pass.
-__global__ void __launch_bounds__(FT) k_fused_pass(float2 *__restrict__ rho, const FPass *__restrict__ passes,
+__global__ void __launch_bounds__(FT, 2) k_fused_pass(float2 *__restrict__ rho, const FPass *__restrict__ passes,
                                                    const FPhase *__restrict__ phases, const float2 *__restrict__ coefs,
                                                    int pass_idx)
 {
@@ -41,6 +42,8 @@ struct CachedPlan {
     std::vector<FPass> hpass;
     std::vector<int> grid;  // tiles per pass
     std::vector<size_t> smem;
+    std::vector<char> pipe;  // pass runs on the persistent double-buffered kernel
+    std::vector<size_t> pipe_smem;
     char *dbuf = nullptr;  // device copy of passes | phases | coefs
     size_t phase_off = 0, coef_off = 0;
     long long last_use = 0;
@@ -89,6 +92,85 @@ static bool same_ops(const std::vector<QOp> &a, const std::vector<QOp> &ops, siz
     return true;
 }
 
+// Persistent, double-buffered form: one CTA of kPipeThreads per SM walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; while it applies the phases to tile j (all the
+// pass's superoperators are staged in shared memory once), the cp.async copy of tile j+1 is
+// already in flight, so the HBM traffic overlaps the FP32 work.
+constexpr int kPipeThreads = 512;
+constexpr int kPipeCoefMax = 24 * 256;  // staged coefficients (24 two-qubit phases, 48 KiB)
+constexpr int kPipePhaseMax = 64;
+
+static size_t pipe_smem_bytes(int TB, int L)
+{
+    return 2 * ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + sizeof(float2) * kPipeCoefMax +
+           sizeof(FPhase) * kPipePhaseMax;
+}
+
+__device__ __forceinline__ void pipe_issue(const float2 *__restrict__ rho, const FPass &P, uint64_t t,
+                                           float2 *__restrict__ buf, const uint64_t *__restrict__ hoff)
+{
+    const int TB = P.TB, L = P.L;
+    const uint64_t base = tile_base(P, t);
+    const unsigned nvec = 1u << (TB - 1);
+    const unsigned lmask = (1u << L) - 1u;
+    for (unsigned v = threadIdx.x; v < nvec; v += kPipeThreads) {
+        unsigned e = 2 * v;
+        cp_async16(&buf[e], rho + base + hoff[e >> L] + (e & lmask));
+    }
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1) k_fused_pipe(float2 *__restrict__ rho, const FPass *__restrict__ passes,
+                                                                const FPhase *__restrict__ phases,
+                                                                const float2 *__restrict__ coefs, int pass_idx,
+                                                                unsigned ntiles)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const FPass &P = passes[pass_idx];
+    const int TB = P.TB, L = P.L;
+    float2 *buf0 = reinterpret_cast<float2 *>(smem);
+    float2 *buf1 = buf0 + (1u << TB);
+    uint64_t *hoff = reinterpret_cast<uint64_t *>(buf1 + (1u << TB));
+    float2 *S = reinterpret_cast<float2 *>(hoff + ((1u << (TB - L)) | 1u) + 1u);
+    FPhase *F = reinterpret_cast<FPhase *>(S + kPipeCoefMax);
+    tile_hoff_nt<kPipeThreads>(P, hoff);
+    // stage the pass's phase headers and coefficients (offsets rebased to the staged copy)
+    const int nph = P.nphase;
+    const int c0 = nph ? phases[P.phase0].coef : 0;
+    int ncoef = 0;
+    if (nph) {
+        const FPhase &last = phases[P.phase0 + nph - 1];
+        ncoef = last.coef + phase_coefs(last.nq) - c0;
+    }
+    for (int i = threadIdx.x; i < nph; i += kPipeThreads) {
+        FPhase f = phases[P.phase0 + i];
+        f.coef -= c0;
+        F[i] = f;
+    }
+    for (int i = threadIdx.x; i < ncoef; i += kPipeThreads) S[i] = coefs[c0 + i];
+    __syncthreads();
+
+    unsigned t = blockIdx.x;
+    if (t < ntiles) pipe_issue(rho, P, t, buf0, hoff);
+    cp_async_commit();
+    for (unsigned j = 0; t < ntiles; j++, t += gridDim.x) {
+        float2 *cur = (j & 1) ? buf1 : buf0;
+        float2 *nxt = (j & 1) ? buf0 : buf1;
+        const unsigned tn = t + gridDim.x;
+        if (tn < ntiles) pipe_issue(rho, P, tn, nxt, hoff);
+        cp_async_commit();
+        cp_async_wait_group1();  // everything but the newest group: tile t has landed
+        __syncthreads();
+        for (int ph = 0; ph < nph; ph++) {
+            const FPhase f = F[ph];
+            tile_apply_phase<kPipeThreads>(cur, TB, f, S + f.coef);
+            __syncthreads();
+        }
+        tile_store_nt<kPipeThreads>(rho, P, t, cur, hoff);
+        __syncthreads();  // cur is refilled two iterations later
+    }
+    cp_async_wait_all();
+}
+
 static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, size_t e, int k, int tbmax,
                              CachedPlan &cp)
 {
@@ -97,7 +179,15 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
     append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp);
     cp.hpass = tp.passes;
     cp.smem = tp.smem;
-    for (const FPass &fp : tp.passes) cp.grid.push_back(1 << fp.nother);
+    for (const FPass &fp : tp.passes) {
+        cp.grid.push_back(1 << fp.nother);
+        int ncoef = 0;
+        for (int i = 0; i < fp.nphase; i++) ncoef += phase_coefs(tp.phases[fp.phase0 + i].nq);
+        const bool ok = fp.TB >= 12 && (1 << fp.nother) >= 4 * c->nsm && fp.nphase <= kPipePhaseMax &&
+                        ncoef <= kPipeCoefMax;
+        cp.pipe.push_back(ok ? 1 : 0);
+        cp.pipe_smem.push_back(pipe_smem_bytes(fp.TB, fp.L));
+    }
     size_t sz_pass = sizeof(FPass) * tp.passes.size();
     cp.phase_off = (sz_pass + 255) & ~(size_t)255;
     size_t sz_ph = sizeof(FPhase) * tp.phases.size();
@@ -168,9 +258,13 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     }
     hit->last_use = ++rt->tick;
 
-    size_t maxsm = 0;
-    for (size_t s : hit->smem) maxsm = s > maxsm ? s : maxsm;
+    size_t maxsm = 0, maxpipe = 0;
+    for (size_t p = 0; p < hit->smem.size(); p++) {
+        if (hit->pipe[p]) maxpipe = std::max(maxpipe, hit->pipe_smem[p]);
+        else maxsm = std::max(maxsm, hit->smem[p]);
+    }
     qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
+    if (!sst && maxpipe) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pipe), maxpipe);
     if (sst) return sst;
     const FPass *dp = reinterpret_cast<const FPass *>(hit->dbuf);
     const FPhase *dph = reinterpret_cast<const FPhase *>(hit->dbuf + hit->phase_off);
@@ -187,7 +281,13 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             }
             cudaEventRecord(e0, c->stream);
         }
-        k_fused_pass<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
+        if (hit->pipe[p]) {
+            const unsigned ntiles = (unsigned)hit->grid[p];
+            const unsigned g = std::min<unsigned>(ntiles, (unsigned)c->nsm);
+            k_fused_pipe<<<g, kPipeThreads, hit->pipe_smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p, ntiles);
+        } else {
+            k_fused_pass<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
+        }
         c->launches++;
         c->passes++;
         if (c->timing) {

@@ -208,12 +208,27 @@ std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, siz
                     else ph.qb = q;
                 }
             ph.nops = (int)pch.size();
-            if (!count_only) {
+            bool linked = false;  // does a two-qubit op tie the phase's qubits together?
+            for (size_t i : pch) linked |= ops[i].k == 2;
+            ph.product = ph.nq == 2 && !linked;
+            if (count_only) {
+                identity(ph.S, 0);
+            } else if (ph.product) {
+                // ops on different qubits commute: compose each qubit's ops on their own
+                std::vector<c128> sa, sb;
+                for (int side = 0; side < 2; side++) {
+                    const int qq = side == 0 ? ph.qa : ph.qb;
+                    acc.start(1, qq, -1);
+                    for (size_t i : pch)
+                        if (ops[i].qubits[0] == qq) acc.add(ops[i]);
+                    acc.result(side == 0 ? sa : sb);
+                }
+                ph.S = sa;
+                ph.S.insert(ph.S.end(), sb.begin(), sb.end());
+            } else {
                 acc.start(ph.nq, ph.qa, ph.qb);
                 for (size_t i : pch) acc.add(ops[i]);
                 acc.result(ph.S);
-            } else {
-                identity(ph.S, 0);
             }
             pp.phases.push_back(std::move(ph));
             prem.swap(prest);

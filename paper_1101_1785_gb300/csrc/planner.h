@@ -11,8 +11,10 @@ namespace qcw {
 
 struct PhasePlan {
     int nq;                 // 1 or 2
+    bool product = false;   // nq == 2 with no two-qubit op: S = S_a (x) S_b
     int qa, qb;             // phase qubits (qb = -1 when nq == 1)
-    std::vector<c128> S;    // composed superoperator, 4x4 (nq = 1) or 16x16 (nq = 2)
+    std::vector<c128> S;    // composed superoperator: 4x4 (nq = 1), 16x16 (nq = 2),
+                            // or S_a then S_b, 4x4 each (product)
     int nops;               // operations folded into S
 };
 

@@ -47,14 +47,15 @@ void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TileP
         fp.phase0 = (int)out.phases.size();
         for (const PhasePlan &ph : pp.phases) {
             FPhase f{};
-            f.nq = ph.nq;
+            f.nq = ph.nq == 1 ? PH_ONE : ph.product ? PH_PRODUCT : PH_TWO;
             f.coef = (int)out.coefs.size();
             if (ph.nq == 2) {
                 f.pos[0] = (int8_t)tile_pos(fp, 2 * n - 1 - ph.qa);
                 f.pos[1] = (int8_t)tile_pos(fp, 2 * n - 1 - ph.qb);
                 f.pos[2] = (int8_t)tile_pos(fp, n - 1 - ph.qa);
                 f.pos[3] = (int8_t)tile_pos(fp, n - 1 - ph.qb);
-                out.nphase2++;
+                if (ph.product) out.nphasep++;
+                else out.nphase2++;
             } else {
                 f.pos[0] = (int8_t)tile_pos(fp, 2 * n - 1 - ph.qa);
                 f.pos[1] = (int8_t)tile_pos(fp, n - 1 - ph.qa);

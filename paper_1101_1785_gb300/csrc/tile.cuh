@@ -20,6 +20,8 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 __device__ __forceinline__ unsigned ins0u(unsigned x, int p)
 {
@@ -29,7 +31,7 @@ __device__ __forceinline__ unsigned ins0u(unsigned x, int p)
 
 // Two-qubit phase: 16x16 superoperator S (shared memory, row-major) on every group.
 // G groups per thread share each coefficient load.
-template <int G>
+template <int G, int NT = kTileThreads>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
 {
@@ -42,12 +44,12 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
             if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
     const unsigned ng = 1u << (TB - 4);
     const float4 *S4 = reinterpret_cast<const float4 *>(S);
-    for (unsigned g0 = threadIdx.x; g0 < ng; g0 += G * kTileThreads) {
+    for (unsigned g0 = threadIdx.x; g0 < ng; g0 += G * NT) {
         unsigned base[G];
         float2 x[G][16];
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            unsigned g = g0 + j * kTileThreads;
+            unsigned g = g0 + j * NT;
             base[j] = ins0u(ins0u(ins0u(ins0u(g, p[0]), p[1]), p[2]), p[3]);
 #pragma unroll
             for (int e = 0; e < 16; e++)
@@ -79,6 +81,7 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
 }
 
 // One-qubit phase: 4x4 superoperator on every (row pair x column pair) group.
+template <int NT = kTileThreads>
 __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
 {
@@ -89,7 +92,7 @@ __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, c
 #pragma unroll
     for (int i = 0; i < 16; i++) s[i] = S[i];
     const unsigned ng = 1u << (TB - 2);
-    for (unsigned g = threadIdx.x; g < ng; g += kTileThreads) {
+    for (unsigned g = threadIdx.x; g < ng; g += NT) {
         unsigned b = ins0u(ins0u(g, lo), hi);
         float2 x[4] = {tile[b], tile[b + dc], tile[b + dr], tile[b + dr + dc]};
         float2 y[4];
@@ -103,6 +106,83 @@ __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, c
         tile[b + dc] = y[1];
         tile[b + dr] = y[2];
         tile[b + dr + dc] = y[3];
+    }
+}
+
+// y = s x on one quartet (e = 2 r + c) of a 16-member group, members m0..m3.
+__device__ __forceinline__ void quartet4(const float2 (&s)[16], float2 (&x)[16], int m0, int m1, int m2, int m3)
+{
+    const float2 a = x[m0], b = x[m1], c = x[m2], d = x[m3];
+    float2 y[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        y[e] = make_float2(0.f, 0.f);
+        cfma(y[e], s[4 * e + 0], a);
+        cfma(y[e], s[4 * e + 1], b);
+        cfma(y[e], s[4 * e + 2], c);
+        cfma(y[e], s[4 * e + 3], d);
+    }
+    x[m0] = y[0];
+    x[m1] = y[1];
+    x[m2] = y[2];
+    x[m3] = y[3];
+}
+
+// Product phase: two one-qubit superoperators (S_a on (r_a, c_a), then S_b on (r_b, c_b);
+// they commute) on every 16-member group, in one shared-memory round trip.  Member
+// index e = 8 r_a + 4 r_b + 2 c_a + c_b.
+template <int NT = kTileThreads>
+__device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int TB, const FPhase &F,
+                                                const float2 *__restrict__ S)
+{
+    const unsigned d0 = 1u << F.pos[0], d1 = 1u << F.pos[1], d2 = 1u << F.pos[2], d3 = 1u << F.pos[3];
+    int p[4] = {F.pos[0], F.pos[1], F.pos[2], F.pos[3]};
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = a + 1; b < 4; b++)
+            if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
+    const unsigned ng = 1u << (TB - 4);
+    for (unsigned g = threadIdx.x; g < ng; g += NT) {
+        const unsigned base = ins0u(ins0u(ins0u(ins0u(g, p[0]), p[1]), p[2]), p[3]);
+        float2 x[16];
+#pragma unroll
+        for (int e = 0; e < 16; e++)
+            x[e] = tile[base + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u)];
+        float2 s[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) s[i] = S[i];
+#pragma unroll
+        for (int o = 0; o < 4; o++) {  // o = (r_b, c_b)
+            const int rb = o >> 1, cb = o & 1;
+            quartet4(s, x, 4 * rb + cb, 4 * rb + 2 + cb, 8 + 4 * rb + cb, 8 + 4 * rb + 2 + cb);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i++) s[i] = S[16 + i];
+#pragma unroll
+        for (int o = 0; o < 4; o++) {  // o = (r_a, c_a)
+            const int ra = o >> 1, ca = o & 1;
+            quartet4(s, x, 8 * ra + 2 * ca, 8 * ra + 2 * ca + 1, 8 * ra + 4 + 2 * ca, 8 * ra + 4 + 2 * ca + 1);
+        }
+#pragma unroll
+        for (int e = 0; e < 16; e++)
+            tile[base + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u)] = x[e];
+    }
+}
+
+// Apply one phase whose coefficients are at S (shared or global memory).
+template <int NT = kTileThreads>
+__device__ __forceinline__ void tile_apply_phase(float2 *__restrict__ tile, int TB, const FPhase &F,
+                                                 const float2 *__restrict__ S)
+{
+    if (F.nq == PH_TWO) {
+        constexpr int kLogNT = NT == 128 ? 7 : NT == 256 ? 8 : NT == 512 ? 9 : 10;
+        if (TB - 4 >= kLogNT + 1) tile_phase2<2, NT>(tile, TB, F, S);  // >= 2 groups per thread
+        else tile_phase2<1, NT>(tile, TB, F, S);
+    } else if (F.nq == PH_PRODUCT) {
+        tile_phase_prod<NT>(tile, TB, F, S);
+    } else {
+        tile_phase1<NT>(tile, TB, F, S);
     }
 }
 
@@ -123,6 +203,17 @@ __device__ __forceinline__ TileSmem tile_smem(unsigned char *smem, int TB, int L
 }
 
 // Offsets (relative to the tile base) of the 2^(TB-L) contiguous runs of a tile.
+template <int NT>
+__device__ __forceinline__ void tile_hoff_nt(const FPass &P, uint64_t *hoff)
+{
+    const int TB = P.TB, L = P.L;
+    for (unsigned i = threadIdx.x; i < (1u << (TB - L)); i += NT) {
+        uint64_t o = 0;
+        for (int j = 0; j < TB - L; j++) o |= (uint64_t)((i >> j) & 1u) << P.tbits[L + j];
+        hoff[i] = o;
+    }
+}
+
 __device__ __forceinline__ void tile_hoff(const FPass &P, uint64_t *hoff)
 {
     const int TB = P.TB, L = P.L;
@@ -163,23 +254,33 @@ __device__ __forceinline__ void tile_load(const float2 *__restrict__ rho, const 
     __syncthreads();
 }
 
-// Apply the phases of pass P to the tile in shared memory.
+// Apply the phases of pass P to the tile in shared memory (coefficients staged per phase).
 __device__ __forceinline__ void tile_phases(const FPass &P, const FPhase *__restrict__ phases,
                                             const float2 *__restrict__ coefs, const TileSmem &sm)
 {
     const int TB = P.TB;
     for (int ph = 0; ph < P.nphase; ph++) {
         const FPhase F = phases[P.phase0 + ph];
-        const int ncoef = F.nq == 2 ? 256 : 16;
+        const int ncoef = phase_coefs(F.nq);
         for (int i = threadIdx.x; i < ncoef; i += kTileThreads) sm.S[i] = coefs[F.coef + i];
         __syncthreads();
-        if (F.nq == 2) {
-            if (TB >= 13) tile_phase2<2>(sm.tile, TB, F, sm.S);
-            else tile_phase2<1>(sm.tile, TB, F, sm.S);
-        } else {
-            tile_phase1(sm.tile, TB, F, sm.S);
-        }
+        tile_apply_phase(sm.tile, TB, F, sm.S);
         __syncthreads();
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void tile_store_nt(float2 *__restrict__ rho, const FPass &P, uint64_t t,
+                                              const float2 *__restrict__ tile, const uint64_t *__restrict__ hoff)
+{
+    const int TB = P.TB, L = P.L;
+    const uint64_t base = tile_base(P, t);
+    const unsigned nvec = 1u << (TB - 1);
+    const unsigned lmask = (1u << L) - 1u;
+    const float4 *t4 = reinterpret_cast<const float4 *>(tile);
+    for (unsigned v = threadIdx.x; v < nvec; v += NT) {
+        unsigned e = 2 * v;
+        *reinterpret_cast<float4 *>(rho + base + hoff[e >> L] + (e & lmask)) = t4[v];
     }
 }
 

@@ -7,6 +7,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <cuda_runtime.h>
+
 #include <vector>
 
 #include "planner.h"
@@ -24,12 +26,17 @@ struct FPass {
     int8_t obits[40];  // virtual bits outside the tile (ascending)
 };
 
+enum : int { PH_ONE = 1, PH_TWO = 2, PH_PRODUCT = 3 };
+
 struct FPhase {
-    int nq;            // 1 or 2
-    int coef;          // offset of the superoperator in the coefficient array (float2 units)
-    int8_t pos[4];     // tile positions of (r_a, r_b, c_a, c_b); (r_a, c_a) when nq == 1
+    int nq;            // PH_ONE (4x4), PH_TWO (16x16) or PH_PRODUCT (two 4x4: S_a then S_b)
+    int coef;          // offset of the superoperator(s) in the coefficient array (float2 units)
+    int8_t pos[4];     // tile positions of (r_a, r_b, c_a, c_b); (r_a, c_a) for PH_ONE
     int pad;
 };
+
+// Coefficients of a phase kind.
+__host__ __device__ inline int phase_coefs(int nq) { return nq == PH_TWO ? 256 : nq == PH_PRODUCT ? 32 : 16; }
 
 constexpr int kTileThreads = 256;  // threads per CTA of the tile kernels
 constexpr int kTileBitsMax = 14;   // largest tile: 2^14 complex64 = 128 KiB
@@ -40,7 +47,7 @@ struct TilePlan {
     std::vector<FPhase> phases;
     std::vector<float2> coefs;
     std::vector<size_t> smem;  // dynamic shared memory per pass
-    int nphase2 = 0, nphase1 = 0;
+    int nphase2 = 0, nphase1 = 0, nphasep = 0;
 };
 
 // Append the passes of `plan` (an n-qubit register, tiles of at most tbmax bits) to `out`.

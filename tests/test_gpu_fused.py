@@ -188,3 +188,11 @@ def test_contexts_of_different_sizes_interleave(q):
         assert np.abs(d.get_state() - oracle.run_circuit(c)).max() <= ATOL
     db.close()
     ds.close()
+
+
+def test_persistent_pipeline_matches_plain_n12(q):
+    """n = 12 has 2^11 tiles per pass, enough for the persistent double-buffered kernel."""
+    c = wl.random_circuit(12, 150, 1212, "mixed", "adpd")
+    a = _run(q, c, q.QCW_MODE_PLAIN).get_state()
+    f = _run(q, c, q.QCW_MODE_FUSED, 5).get_state()
+    assert np.abs(a - f).max() <= 1e-6
