@@ -82,6 +82,15 @@ QCW_API qcw_status qcw_destroy(qcw_ctx *ctx);
  * flushes queued work first. */
 QCW_API qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k);
 
+/* Which kernel runs large fused passes: AUTO (the persistent double-buffered kernel when the
+ * pass has enough tiles and its superoperators fit shared memory, else one CTA per tile),
+ * TILE (always one CTA per tile) or PIPE (persistent whenever the pass qualifies).  Results
+ * are identical; only speed differs.  Flushes queued work first. */
+#define QCW_FUSED_KERNEL_AUTO 0
+#define QCW_FUSED_KERNEL_TILE 1
+#define QCW_FUSED_KERNEL_PIPE 2
+QCW_API qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which);
+
 /* Device pointer of rho and the context's stream (borrowed; valid until destroy). */
 QCW_API qcw_status qcw_get_device_state(qcw_ctx *ctx, void **dev_rho, void **cuda_stream);
 

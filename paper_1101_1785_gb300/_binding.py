@@ -39,6 +39,7 @@ SIGNATURES = {
     "qcw_create_from_ptr": (I, [I, P, P, PP]),
     "qcw_destroy": (I, [P]),
     "qcw_set_mode": (I, [P, I, I]),
+    "qcw_set_fused_kernel": (I, [P, I]),
     "qcw_get_device_state": (I, [P, PP, PP]),
     "qcw_nqubits": (I, [P]),
     "qcw_reset": (I, [P]),
@@ -203,6 +204,10 @@ class Density:
     # ---------------------------------------------------------------- configuration / state
     def set_mode(self, mode: int, fuse_k: int = 0):
         check(lib().qcw_set_mode(self.h, int(mode), int(fuse_k)), "qcw_set_mode")
+
+    def set_fused_kernel(self, which: int):
+        """0 = auto, 1 = one CTA per tile, 2 = persistent double-buffered."""
+        check(lib().qcw_set_fused_kernel(self.h, int(which)), "qcw_set_fused_kernel")
 
     def device_state(self):
         r, s = P(), P()

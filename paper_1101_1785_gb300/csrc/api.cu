@@ -306,6 +306,16 @@ extern "C" qcw_status qcw_destroy(qcw_ctx *ctx)
 
 extern "C" int qcw_nqubits(const qcw_ctx *ctx) { return ctx ? ctx->n : -1; }
 
+extern "C" qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which)
+{
+    CHECK_CTX(ctx);
+    if (which < QCW_FUSED_KERNEL_AUTO || which > QCW_FUSED_KERNEL_PIPE) return set_error(QCW_EINVAL, "bad kernel choice");
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    ctx->fused_kernel = which;
+    return QCW_OK;
+}
+
 extern "C" qcw_status qcw_get_device_state(qcw_ctx *ctx, void **dev_rho, void **cuda_stream)
 {
     CHECK_CTX(ctx);

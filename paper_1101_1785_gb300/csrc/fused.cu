@@ -96,7 +96,7 @@ static bool same_ops(const std::vector<QOp> &a, const std::vector<QOp> &ops, siz
 // blockIdx.x, blockIdx.x + gridDim.x, ...; while it applies the phases to tile j (all the
 // pass's superoperators are staged in shared memory once), the cp.async copy of tile j+1 is
 // already in flight, so the HBM traffic overlaps the FP32 work.
-constexpr int kPipeThreads = 512;
+constexpr int kPipeThreads = 256;
 constexpr int kPipeCoefMax = 24 * 256;  // staged coefficients (24 two-qubit phases, 48 KiB)
 constexpr int kPipePhaseMax = 64;
 
@@ -183,8 +183,9 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
         cp.grid.push_back(1 << fp.nother);
         int ncoef = 0;
         for (int i = 0; i < fp.nphase; i++) ncoef += phase_coefs(tp.phases[fp.phase0 + i].nq);
-        const bool ok = fp.TB >= 12 && (1 << fp.nother) >= 4 * c->nsm && fp.nphase <= kPipePhaseMax &&
-                        ncoef <= kPipeCoefMax;
+        const bool fits = fp.TB >= 12 && (1 << fp.nother) >= 4 * c->nsm && fp.nphase <= kPipePhaseMax &&
+                          ncoef <= kPipeCoefMax;
+        const bool ok = fits && c->fused_kernel != QCW_FUSED_KERNEL_TILE;
         cp.pipe.push_back(ok ? 1 : 0);
         cp.pipe_smem.push_back(pipe_smem_bytes(fp.TB, fp.L));
     }
@@ -225,7 +226,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     int k = c->fuse_k ? c->fuse_k : auto_k(n);
     if (k > n) k = n;
     const int tbmax = 13;
-    uint64_t h = hash_ops(c->queue, b, e, n, k, tbmax);
+    uint64_t h = hash_ops(c->queue, b, e, n, k, tbmax) ^ (0x9e3779b97f4a7c15ull * (uint64_t)(c->fused_kernel + 1));
     CachedPlan *hit = nullptr;
     for (CachedPlan &cp : rt->cache)
         if (cp.hash == h && cp.n == n && cp.k == k && cp.tb == tbmax && same_ops(cp.ops, c->queue, b, e)) {

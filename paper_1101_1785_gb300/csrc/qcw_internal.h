@@ -102,6 +102,7 @@ struct qcw_ctx {
     bool owns_stream = false;
     int mode = QCW_MODE_PLAIN;
     int fuse_k = 0;
+    int fused_kernel = QCW_FUSED_KERNEL_AUTO;
     // reduction scratch: per-block partials and a small result block (+ pinned mirror)
     double *d_partials = nullptr;
     int red_blocks = 0;

@@ -61,21 +61,22 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
 #pragma unroll 1
         for (int e = 0; e < 16; e++) {
             const unsigned oe = ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u);
-            float2 y[G];
+            // two partial sums per output (even / odd inputs) halve the dependent FMA chain
+            float2 y0[G], y1[G];
 #pragma unroll
-            for (int j = 0; j < G; j++) y[j] = make_float2(0.f, 0.f);
+            for (int j = 0; j < G; j++) y0[j] = y1[j] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int f = 0; f < 16; f += 2) {
                 float4 c = S4[8 * e + (f >> 1)];
                 float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
 #pragma unroll
                 for (int j = 0; j < G; j++) {
-                    cfma(y[j], c0, x[j][f]);
-                    cfma(y[j], c1, x[j][f + 1]);
+                    cfma(y0[j], c0, x[j][f]);
+                    cfma(y1[j], c1, x[j][f + 1]);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < G; j++) tile[base[j] + oe] = y[j];
+            for (int j = 0; j < G; j++) tile[base[j] + oe] = cadd(y0[j], y1[j]);
         }
     }
 }
