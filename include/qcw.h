@@ -82,13 +82,18 @@ QCW_API qcw_status qcw_destroy(qcw_ctx *ctx);
  * flushes queued work first. */
 QCW_API qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k);
 
-/* Which kernel runs large fused passes: AUTO (the persistent double-buffered kernel when the
- * pass has enough tiles and its superoperators fit shared memory, else one CTA per tile),
- * TILE (always one CTA per tile) or PIPE (persistent whenever the pass qualifies).  Results
- * are identical; only speed differs.  Flushes queued work first. */
+/* Which kernel runs fused passes.
+ *   HERM (and AUTO, the default): rho is a density matrix, hence Hermitian (Sec. 5.2, rho^dagger
+ *     = rho).  Tiles hold the row and column bits of the same qubits; each pass evolves the
+ *     tiles on or above the diagonal and writes the others as their conjugate transposes (half
+ *     the arithmetic).  A non-Hermitian matrix loaded with qcw_set_state is not preserved.
+ *   TILE: one CTA per tile, no symmetry assumed.
+ *   PIPE: persistent double-buffered CTAs, no symmetry assumed.
+ * Flushes queued work first. */
 #define QCW_FUSED_KERNEL_AUTO 0
 #define QCW_FUSED_KERNEL_TILE 1
 #define QCW_FUSED_KERNEL_PIPE 2
+#define QCW_FUSED_KERNEL_HERM 3
 QCW_API qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which);
 
 /* Device pointer of rho and the context's stream (borrowed; valid until destroy). */

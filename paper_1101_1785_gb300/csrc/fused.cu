@@ -171,21 +171,76 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fused_pipe(float2 *__restri
     cp_async_wait_all();
 }
 
+// Hermitian form (rho = rho^dagger, Sec. 5.2): tiles are symmetric (row and column bits of
+// the same qubits), so the conjugate transpose of the tile with outside bits (o_r, o_c) is
+// the tile (o_c, o_r) and the pass maps it to the conjugate transpose of its own image.  One
+// CTA per unordered pair o_r <= o_c loads, evolves and stores its tile and writes the mirror
+// tile as the conjugate transpose: half the phase arithmetic, 3/4 of the HBM traffic.
+__device__ __forceinline__ void pair_of(unsigned p, unsigned &o_r, unsigned &o_c)
+{
+    unsigned c = (unsigned)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+    while ((c + 1) * (c + 2) / 2 <= p) c++;
+    while (c * (c + 1) / 2 > p) c--;
+    o_c = c;
+    o_r = p - c * (c + 1) / 2;
+}
+
+__global__ void __launch_bounds__(FT, 2) k_fused_herm(float2 *__restrict__ rho, const FPass *__restrict__ passes,
+                                                      const FPhase *__restrict__ phases,
+                                                      const float2 *__restrict__ coefs, int pass_idx)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const FPass &P = passes[pass_idx];
+    const int TB = P.TB, L = P.L, h = P.TB / 2, m = P.nother / 2;
+    const TileSmem sm = tile_smem(smem, TB, L);
+    tile_hoff(P, sm.hoff);
+    unsigned o_r, o_c;
+    pair_of(blockIdx.x, o_r, o_c);
+    __syncthreads();
+    // outside bits ascend: m column bits (o_c) below m row bits (o_r)
+    const uint64_t t_self = ((uint64_t)o_r << m) | o_c;
+    tile_process(rho, P, t_self, phases, coefs, sm);
+    if (o_r == o_c) return;
+    // mirror tile: element t' holds conj(tile[swap(t')]), swap exchanging the column half and
+    // the row half of the tile index.  Adjacent lanes take adjacent elements of one contiguous
+    // run (32-byte segments) and walk the tile's rows in the other lane bits, so that the
+    // shared-memory reads spread over the banks.
+    const uint64_t mbase = tile_base(P, ((uint64_t)o_c << m) | o_r);
+    const int J = L < 2 ? L : 2;
+    const unsigned hmask = (1u << h) - 1u, lmask = (1u << L) - 1u, jmask = (1u << J) - 1u;
+    for (unsigned idx = threadIdx.x; idx < (1u << TB); idx += FT) {
+        const unsigned j = idx & jmask, u = idx >> J;
+        const unsigned Rp = u & hmask, Chi = u >> h;
+        const unsigned tp = (Rp << h) | (Chi << J) | j;
+        const unsigned ts = (((Chi << J) | j) << h) | Rp;
+        const float2 v = sm.tile[ts];
+        rho[mbase + sm.hoff[tp >> L] + (tp & lmask)] = make_float2(v.x, -v.y);
+    }
+}
+
 static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, size_t e, int k, int tbmax,
                              CachedPlan &cp)
 {
     const int n = c->n;
     TilePlan tp;
-    append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp);
+    const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM;
+    append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp, herm);
     cp.hpass = tp.passes;
     cp.smem = tp.smem;
     for (const FPass &fp : tp.passes) {
+        if (fp.herm) {
+            const unsigned long long M = 1ull << (fp.nother / 2);
+            cp.grid.push_back((int)(M * (M + 1) / 2));
+            cp.pipe.push_back(0);
+            cp.pipe_smem.push_back(0);
+            continue;
+        }
         cp.grid.push_back(1 << fp.nother);
         int ncoef = 0;
         for (int i = 0; i < fp.nphase; i++) ncoef += phase_coefs(tp.phases[fp.phase0 + i].nq);
         const bool fits = fp.TB >= 12 && (1 << fp.nother) >= 4 * c->nsm && fp.nphase <= kPipePhaseMax &&
                           ncoef <= kPipeCoefMax;
-        const bool ok = fits && c->fused_kernel != QCW_FUSED_KERNEL_TILE;
+        const bool ok = fits && c->fused_kernel == QCW_FUSED_KERNEL_PIPE;
         cp.pipe.push_back(ok ? 1 : 0);
         cp.pipe_smem.push_back(pipe_smem_bytes(fp.TB, fp.L));
     }
@@ -225,7 +280,8 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     const int n = c->n;
     int k = c->fuse_k ? c->fuse_k : auto_k(n);
     if (k > n) k = n;
-    const int tbmax = 13;
+    const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM;
+    const int tbmax = herm ? 12 : 13;
     uint64_t h = hash_ops(c->queue, b, e, n, k, tbmax) ^ (0x9e3779b97f4a7c15ull * (uint64_t)(c->fused_kernel + 1));
     CachedPlan *hit = nullptr;
     for (CachedPlan &cp : rt->cache)
@@ -265,6 +321,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
         else maxsm = std::max(maxsm, hit->smem[p]);
     }
     qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
+    if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm), maxsm);
     if (!sst && maxpipe) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pipe), maxpipe);
     if (sst) return sst;
     const FPass *dp = reinterpret_cast<const FPass *>(hit->dbuf);
@@ -282,7 +339,9 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             }
             cudaEventRecord(e0, c->stream);
         }
-        if (hit->pipe[p]) {
+        if (hit->hpass[p].herm) {
+            k_fused_herm<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
+        } else if (hit->pipe[p]) {
             const unsigned ntiles = (unsigned)hit->grid[p];
             const unsigned g = std::min<unsigned>(ntiles, (unsigned)c->nsm);
             k_fused_pipe<<<g, kPipeThreads, hit->pipe_smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p, ntiles);

@@ -10,7 +10,7 @@ size_t tile_smem_bytes(int TB, int L)
 
 // Tile bits of a pass: rows and columns of Q, then the lowest column bits until tbmax bits
 // (or all column bits are in).
-static void tile_layout(const std::vector<int> &Q, int n, int tbmax, FPass &fp)
+static void tile_layout(const std::vector<int> &Q, int n, int tbmax, FPass &fp, bool herm)
 {
     uint64_t in = 0;
     for (int q : Q) {
@@ -18,7 +18,13 @@ static void tile_layout(const std::vector<int> &Q, int n, int tbmax, FPass &fp)
         in |= 1ull << (2 * n - 1 - q);
     }
     int want = tbmax < 2 * n ? tbmax : 2 * n;
-    for (int v = 0; v < n && __builtin_popcountll(in) < want; v++) in |= 1ull << v;
+    if (herm) {  // add whole qubits, lowest first: column bit v and row bit n + v together
+        want &= ~1;
+        for (int v = 0; v < n && __builtin_popcountll(in) < want; v++) in |= (1ull << v) | (1ull << (n + v));
+    } else {
+        for (int v = 0; v < n && __builtin_popcountll(in) < want; v++) in |= 1ull << v;
+    }
+    fp.herm = herm ? 1 : 0;
     int tb = 0, ob = 0;
     for (int v = 0; v < 2 * n; v++) {
         if (in & (1ull << v)) fp.tbits[tb++] = (int8_t)v;
@@ -38,11 +44,11 @@ static int tile_pos(const FPass &fp, int vbit)
     return -1;
 }
 
-void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TilePlan &out)
+void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TilePlan &out, bool herm)
 {
     for (const PassPlan &pp : plan) {
         FPass fp{};
-        tile_layout(pp.Q, n, tbmax, fp);
+        tile_layout(pp.Q, n, tbmax, fp, herm);
         fp.nphase = (int)pp.phases.size();
         fp.phase0 = (int)out.phases.size();
         for (const PhasePlan &ph : pp.phases) {

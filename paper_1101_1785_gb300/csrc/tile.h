@@ -21,7 +21,7 @@ struct FPass {
     int nother;        // 2n - TB
     int nphase;
     int phase0;        // first phase in the phase array
-    int pad;
+    int herm;          // symmetric tile: the same qubits' row and column bits (Hermitian kernel)
     int8_t tbits[16];  // virtual bit of tile bit j (ascending)
     int8_t obits[40];  // virtual bits outside the tile (ascending)
 };
@@ -51,7 +51,10 @@ struct TilePlan {
 };
 
 // Append the passes of `plan` (an n-qubit register, tiles of at most tbmax bits) to `out`.
-void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TilePlan &out);
+// With herm, every tile holds the row and the column bits of the same qubits (Q plus the
+// lowest qubits outside Q, tbmax / 2 qubits in all), so that the conjugate transpose of a
+// tile is again a tile of the pass.
+void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TilePlan &out, bool herm = false);
 
 // Dynamic shared memory of a tile kernel for a pass with TB tile bits and an L-bit run.
 size_t tile_smem_bytes(int TB, int L);

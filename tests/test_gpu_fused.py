@@ -196,3 +196,23 @@ def test_persistent_pipeline_matches_plain_n12(q):
     a = _run(q, c, q.QCW_MODE_PLAIN).get_state()
     f = _run(q, c, q.QCW_MODE_FUSED, 5).get_state()
     assert np.abs(a - f).max() <= 1e-6
+
+
+@pytest.mark.parametrize("n", [8, 11])
+def test_hermitian_kernel_matches_general_kernels(q, n):
+    """The Hermitian pass kernel (tiles on or above the diagonal, mirrors written as conjugate
+    transposes) against the general per-tile kernel and, at n = 8, the oracle."""
+    c = wl.random_circuit(n, 80, 808 + n, "mixed", "adpd")
+    got = {}
+    for which in (1, 3):
+        d = q.Density(n)
+        d.set_mode(q.QCW_MODE_FUSED, 5)
+        d.set_fused_kernel(which)
+        for op in c.ops:
+            d.apply_op(op)
+        got[which] = d.get_state()
+        d.close()
+    assert np.abs(got[3] - got[1]).max() <= 1e-6
+    assert np.abs(got[3] - got[3].conj().T).max() <= 1e-7
+    if n == 8:
+        assert np.abs(got[3] - oracle.run_circuit(c)).max() <= ATOL
