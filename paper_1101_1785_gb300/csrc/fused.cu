@@ -21,6 +21,17 @@ namespace qcw {
 
 constexpr int FT = kTileThreads;
 
+// Parameter block of the Hermitian kernel that reads its superoperators from the constant bank.
+constexpr int kParamPhaseMax = 24;
+constexpr int kParamCoefMax = 3520;  // float2: the whole block stays under the 32 KiB limit
+
+struct PassParams {
+    FPass pass;
+    FPhase phases[kParamPhaseMax];
+    float2 coefs[kParamCoefMax];
+};
+
+
 // One CTA per tile of one pass.
 __global__ void __launch_bounds__(FT, 2) k_fused_pass(float2 *__restrict__ rho, const FPass *__restrict__ passes,
                                                    const FPhase *__restrict__ phases, const float2 *__restrict__ coefs,
@@ -44,6 +55,8 @@ struct CachedPlan {
     std::vector<size_t> smem;
     std::vector<char> pipe;  // pass runs on the persistent double-buffered kernel
     std::vector<size_t> pipe_smem;
+    std::vector<PassParams> params;  // Hermitian passes whose superoperators fit the parameter block
+    std::vector<int> param_idx;      // index into params, or -1
     char *dbuf = nullptr;  // device copy of passes | phases | coefs
     size_t phase_off = 0, coef_off = 0;
     long long last_use = 0;
@@ -218,6 +231,84 @@ __global__ void __launch_bounds__(FT, 2) k_fused_herm(float2 *__restrict__ rho, 
     }
 }
 
+// Same Hermitian pass with the pass's phase headers and superoperators carried in the kernel
+// parameter block (constant bank): every thread reads the same coefficient at the same time,
+// so the reads go through the constant cache instead of competing with the tile's
+// shared-memory traffic.
+__device__ __forceinline__ void cphase2(float2 *__restrict__ tile, int TB, const FPhase &F, const PassParams &pp)
+{
+    const unsigned d0 = 1u << F.pos[0], d1 = 1u << F.pos[1], d2 = 1u << F.pos[2], d3 = 1u << F.pos[3];
+    int p[4] = {F.pos[0], F.pos[1], F.pos[2], F.pos[3]};
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = a + 1; b < 4; b++)
+            if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
+    const unsigned ng = 1u << (TB - 4);
+    for (unsigned g = threadIdx.x; g < ng; g += FT) {
+        const unsigned base = ins0u(ins0u(ins0u(ins0u(g, p[0]), p[1]), p[2]), p[3]);
+        float2 x[16];
+#pragma unroll
+        for (int e = 0; e < 16; e++)
+            x[e] = tile[base + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u)];
+#pragma unroll 2
+        for (int e = 0; e < 16; e++) {
+            const unsigned oe = ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u);
+            const float2 *row = pp.coefs + F.coef + 16 * e;
+            float2 y0 = make_float2(0.f, 0.f), y1 = y0;
+#pragma unroll
+            for (int f = 0; f < 16; f += 2) {
+                cfma(y0, row[f], x[f]);
+                cfma(y1, row[f + 1], x[f + 1]);
+            }
+            tile[base + oe] = cadd(y0, y1);
+        }
+    }
+}
+
+__device__ __forceinline__ void cphase_small(float2 *__restrict__ tile, int TB, const FPhase &F, const PassParams &pp)
+{
+    float2 s[32];
+    const int nc = F.nq == PH_PRODUCT ? 32 : 16;
+#pragma unroll
+    for (int i = 0; i < 32; i++) s[i] = i < nc ? pp.coefs[F.coef + i] : make_float2(0.f, 0.f);
+    if (F.nq == PH_PRODUCT) tile_phase_prod<FT>(tile, TB, F, s);
+    else tile_phase1<FT>(tile, TB, F, s);
+}
+
+__global__ void __launch_bounds__(FT, 2) k_fused_herm_c(float2 *__restrict__ rho, const __grid_constant__ PassParams pp)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const FPass &P = pp.pass;
+    const int TB = P.TB, L = P.L, h = P.TB / 2, m = P.nother / 2;
+    const TileSmem sm = tile_smem(smem, TB, L);
+    tile_hoff(P, sm.hoff);
+    unsigned o_r, o_c;
+    pair_of(blockIdx.x, o_r, o_c);
+    __syncthreads();
+    const uint64_t t_self = ((uint64_t)o_r << m) | o_c;
+    tile_load(rho, P, t_self, sm, false);
+    for (int ph = 0; ph < P.nphase; ph++) {
+        const FPhase F = pp.phases[ph];
+        if (F.nq == PH_TWO) cphase2(sm.tile, TB, F, pp);
+        else cphase_small(sm.tile, TB, F, pp);
+        __syncthreads();
+    }
+    tile_store(rho, P, t_self, sm);
+    if (o_r == o_c) return;
+    const uint64_t mbase = tile_base(P, ((uint64_t)o_c << m) | o_r);
+    const int J = L < 2 ? L : 2;
+    const unsigned hmask = (1u << h) - 1u, lmask = (1u << L) - 1u, jmask = (1u << J) - 1u;
+    for (unsigned idx = threadIdx.x; idx < (1u << TB); idx += FT) {
+        const unsigned j = idx & jmask, u = idx >> J;
+        const unsigned Rp = u & hmask, Chi = u >> h;
+        const unsigned tp = (Rp << h) | (Chi << J) | j;
+        const unsigned ts = (((Chi << J) | j) << h) | Rp;
+        const float2 v = sm.tile[ts];
+        rho[mbase + sm.hoff[tp >> L] + (tp & lmask)] = make_float2(v.x, -v.y);
+    }
+}
+
 static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, size_t e, int k, int tbmax,
                              CachedPlan &cp)
 {
@@ -233,8 +324,25 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
             cp.grid.push_back((int)(M * (M + 1) / 2));
             cp.pipe.push_back(0);
             cp.pipe_smem.push_back(0);
+            int ncoef = 0;
+            for (int i = 0; i < fp.nphase; i++) ncoef += phase_coefs(tp.phases[fp.phase0 + i].nq);
+            if (fp.nphase <= kParamPhaseMax && ncoef <= kParamCoefMax) {
+                PassParams pp{};
+                pp.pass = fp;
+                const int c0 = fp.nphase ? tp.phases[fp.phase0].coef : 0;
+                for (int i = 0; i < fp.nphase; i++) {
+                    pp.phases[i] = tp.phases[fp.phase0 + i];
+                    pp.phases[i].coef -= c0;
+                }
+                for (int i = 0; i < ncoef; i++) pp.coefs[i] = tp.coefs[c0 + i];
+                cp.param_idx.push_back((int)cp.params.size());
+                cp.params.push_back(pp);
+            } else {
+                cp.param_idx.push_back(-1);
+            }
             continue;
         }
+        cp.param_idx.push_back(-1);
         cp.grid.push_back(1 << fp.nother);
         int ncoef = 0;
         for (int i = 0; i < fp.nphase; i++) ncoef += phase_coefs(tp.phases[fp.phase0 + i].nq);
@@ -322,6 +430,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     }
     qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm), maxsm);
+    if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm_c), maxsm);
     if (!sst && maxpipe) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pipe), maxpipe);
     if (sst) return sst;
     const FPass *dp = reinterpret_cast<const FPass *>(hit->dbuf);
@@ -339,7 +448,9 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             }
             cudaEventRecord(e0, c->stream);
         }
-        if (hit->hpass[p].herm) {
+        if (hit->hpass[p].herm && hit->param_idx[p] >= 0) {
+            k_fused_herm_c<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, hit->params[hit->param_idx[p]]);
+        } else if (hit->hpass[p].herm) {
             k_fused_herm<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
         } else if (hit->pipe[p]) {
             const unsigned ntiles = (unsigned)hit->grid[p];
