@@ -189,16 +189,21 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_fused_pipe(float2 *__restri
 // the tile (o_c, o_r) and the pass maps it to the conjugate transpose of its own image.  One
 // CTA per unordered pair o_r <= o_c loads, evolves and stores its tile and writes the mirror
 // tile as the conjugate transpose: half the phase arithmetic, 3/4 of the HBM traffic.
+// Pair p -> (o_r, o_c) with o_r <= o_c, p = o_c (o_c + 1) / 2 + o_r.  FP32 estimate of the
+// triangular root, corrected in integers (FP64 is far slower on this GPU).
 __device__ __forceinline__ void pair_of(unsigned p, unsigned &o_r, unsigned &o_c)
 {
-    unsigned c = (unsigned)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-    while ((c + 1) * (c + 2) / 2 <= p) c++;
-    while (c * (c + 1) / 2 > p) c--;
-    o_c = c;
-    o_r = p - c * (c + 1) / 2;
+    const unsigned long long pp = p;
+    unsigned long long c = (unsigned long long)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+    while ((c + 1) * (c + 2) / 2 <= pp) c++;
+    while (c * (c + 1) / 2 > pp) c--;
+    o_c = (unsigned)c;
+    o_r = (unsigned)(pp - c * (c + 1) / 2);
 }
 
-__global__ void __launch_bounds__(FT, 2) k_fused_herm(float2 *__restrict__ rho, const FPass *__restrict__ passes,
+constexpr int HT = 128;  // threads of the Hermitian kernel: 2^12-element tiles give 2 groups each
+
+__global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, const FPass *__restrict__ passes,
                                                       const FPhase *__restrict__ phases,
                                                       const float2 *__restrict__ coefs, int pass_idx)
 {
@@ -206,13 +211,31 @@ __global__ void __launch_bounds__(FT, 2) k_fused_herm(float2 *__restrict__ rho, 
     const FPass &P = passes[pass_idx];
     const int TB = P.TB, L = P.L, h = P.TB / 2, m = P.nother / 2;
     const TileSmem sm = tile_smem(smem, TB, L);
-    tile_hoff(P, sm.hoff);
+    tile_hoff_nt<HT>(P, sm.hoff);
     unsigned o_r, o_c;
     pair_of(blockIdx.x, o_r, o_c);
     __syncthreads();
     // outside bits ascend: m column bits (o_c) below m row bits (o_r)
     const uint64_t t_self = ((uint64_t)o_r << m) | o_c;
-    tile_process(rho, P, t_self, phases, coefs, sm);
+    {
+        const uint64_t base = tile_base(P, t_self);
+        const unsigned nvec = 1u << (TB - 1), lmask = (1u << L) - 1u;
+        for (unsigned v = threadIdx.x; v < nvec; v += HT) {
+            unsigned e = 2 * v;
+            cp_async16(&sm.tile[e], rho + base + sm.hoff[e >> L] + (e & lmask));
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    for (int ph = 0; ph < P.nphase; ph++) {
+        const FPhase F = phases[P.phase0 + ph];
+        const int ncoef = phase_coefs(F.nq);
+        for (int i = threadIdx.x; i < ncoef; i += HT) sm.S[i] = coefs[F.coef + i];
+        __syncthreads();
+        tile_apply_phase<HT>(sm.tile, TB, F, sm.S);
+        __syncthreads();
+    }
+    tile_store_nt<HT>(rho, P, t_self, sm.tile, sm.hoff);
     if (o_r == o_c) return;
     // mirror tile: element t' holds conj(tile[swap(t')]), swap exchanging the column half and
     // the row half of the tile index.  Adjacent lanes take adjacent elements of one contiguous
@@ -221,7 +244,7 @@ __global__ void __launch_bounds__(FT, 2) k_fused_herm(float2 *__restrict__ rho, 
     const uint64_t mbase = tile_base(P, ((uint64_t)o_c << m) | o_r);
     const int J = L < 2 ? L : 2;
     const unsigned hmask = (1u << h) - 1u, lmask = (1u << L) - 1u, jmask = (1u << J) - 1u;
-    for (unsigned idx = threadIdx.x; idx < (1u << TB); idx += FT) {
+    for (unsigned idx = threadIdx.x; idx < (1u << TB); idx += HT) {
         const unsigned j = idx & jmask, u = idx >> J;
         const unsigned Rp = u & hmask, Chi = u >> h;
         const unsigned tp = (Rp << h) | (Chi << J) | j;
@@ -314,7 +337,8 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
 {
     const int n = c->n;
     TilePlan tp;
-    const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM;
+    const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
+                      c->fused_kernel == QCW_FUSED_KERNEL_HERMC;
     append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp, herm);
     cp.hpass = tp.passes;
     cp.smem = tp.smem;
@@ -388,7 +412,8 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     const int n = c->n;
     int k = c->fuse_k ? c->fuse_k : auto_k(n);
     if (k > n) k = n;
-    const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM;
+    const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
+                      c->fused_kernel == QCW_FUSED_KERNEL_HERMC;
     const int tbmax = herm ? 12 : 13;
     uint64_t h = hash_ops(c->queue, b, e, n, k, tbmax) ^ (0x9e3779b97f4a7c15ull * (uint64_t)(c->fused_kernel + 1));
     CachedPlan *hit = nullptr;
@@ -448,10 +473,10 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             }
             cudaEventRecord(e0, c->stream);
         }
-        if (hit->hpass[p].herm && hit->param_idx[p] >= 0) {
+        if (hit->hpass[p].herm && hit->param_idx[p] >= 0 && c->fused_kernel == QCW_FUSED_KERNEL_HERMC) {
             k_fused_herm_c<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, hit->params[hit->param_idx[p]]);
         } else if (hit->hpass[p].herm) {
-            k_fused_herm<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
+            k_fused_herm<<<hit->grid[p], HT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
         } else if (hit->pipe[p]) {
             const unsigned ntiles = (unsigned)hit->grid[p];
             const unsigned g = std::min<unsigned>(ntiles, (unsigned)c->nsm);
