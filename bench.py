@@ -5,7 +5,7 @@ Workload (one "step"): a 14-qubit density matrix (16384 x 16384 complex64 on the
 starts in |0..0><0..0|; a seeded 1000-gate circuit (kinds uniform over H, X, Z, S, T,
 CNOT, Haar SU(2)) runs with amplitude damping (gamma = 0.01) and phase damping
 (lambda = 0.02) on every touched qubit after each gate, in the fused path (planner +
-fused-pass kernel, fusion width 5).  After every 100 gates the step reads trace and purity
+Hermitian fused-pass kernel, fusion width chosen per segment by the library's cost model).  After every 100 gates the step reads trace and purity
 in FP64; at the end it reads the per-qubit probabilities, measures qubit 0 (u-driven
 projective measurement with renormalisation) and takes the partial trace over qubits 0, 1.
 
@@ -33,7 +33,7 @@ UNIT = "gate-applications/s"
 N_QUBITS = 14
 N_GATES = 1000
 CHUNK = 100
-FUSE_K = 5
+FUSE_K = 0  # 0: the library's cost model picks the width per segment
 U_MEASURE = 0.37
 PT_KEEP = [0, 1]
 
@@ -51,7 +51,7 @@ def parse_args():
                          "one launch; serve: Poisson request stream through the continuous-batching server")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
-    ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "pipe", "herm", "hermc"],
+    ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "pipe", "herm", "hermc", "hermp"],
                     help="kernel for large fused passes (results are identical)")
     ap.add_argument("--fuse-k", type=int, default=FUSE_K, help="qubits per fused pass")
     ap.add_argument("--qubits", type=int, default=N_QUBITS,
@@ -146,9 +146,20 @@ def d2h_bytes_per_step(n):
     return (N_GATES // CHUNK) * (diag + 8) + diag + diag + 16 * (4 ** len(PT_KEEP))
 
 
+def herm_pass_bytes(n, tile_qubits=6):
+    """HBM bytes one Hermitian fused pass must move: read the tiles on or above the diagonal
+    (M (M + 1) / 2 of the M^2 tiles, M = 2^(n - 6)), write every tile (the evolved ones and
+    their conjugate-transpose mirrors).  16 * 4^n when the whole matrix is one tile."""
+    if n <= tile_qubits:
+        return 16 * 4 ** n
+    m = 1 << (n - tile_qubits)
+    tile = 8 * 4 ** tile_qubits
+    return tile * (m * (m + 1) // 2 + m * m)
+
+
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("fused.cu", "planner.cpp", "qcw_device.cuh"):
+    for f in ("fused.cu", "planner.cpp", "qcw_device.cuh", "tile.cuh", "tile.cpp"):
         with open(os.path.join(ROOT, "paper_1101_1785_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -156,7 +167,7 @@ def kernel_hash():
 
 def recorded_traffic():
     """dram bytes per fused-pass launch from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", "fused_pass_n14_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "k_fused_herm_n14_traffic.txt")
     try:
         kv = {}
         with open(path) as f:
@@ -245,7 +256,7 @@ def run_ours(args):
     packed = [q.PackedOps(p) for p in parts]
     d = q.Density(nq)
     d.set_mode(q.QCW_MODE_FUSED, args.fuse_k)
-    d.set_fused_kernel({"auto": 0, "tile": 1, "pipe": 2, "herm": 3, "hermc": 4}[args.fused_kernel])
+    d.set_fused_kernel({"auto": 0, "tile": 1, "pipe": 2, "herm": 3, "hermc": 4, "hermp": 5}[args.fused_kernel])
     rho_ptr, stream_ptr = d.device_state()
     ext = torch.cuda.ExternalStream(stream_ptr)
 
@@ -303,7 +314,7 @@ def run_ours(args):
     e2e_value = total_gates / e2e_s
 
     peaks, peak_kind = load_peaks()
-    per_launch_bytes = 16 * (4 ** nq)
+    per_launch_bytes = herm_pass_bytes(nq)
     avg_ms = st["fused_pass_ms"] / max(1, st["timed_passes"])
     achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
     hbm = float(peaks["hbm_gbs"])
@@ -322,13 +333,13 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": "14-qubit noisy density matrix (16384 x 16384 complex64), seeded "
                                    "1000-gate circuit {H,X,Z,S,T,CNOT,Haar}, AD(0.01)+PD(0.02) per "
-                                   "touched qubit, fused width 5, FP64 trace+purity every 100 gates, "
+                                   "touched qubit, fused (width by cost model), FP64 trace+purity every 100 gates, "
                                    "probabilities, measurement, partial trace",
                        "qubits": nq, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({8 * 4 ** nq / 2**20:.0f} MiB rho vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": recorded_traffic(),
-                         "peak_kind": peak_kind, "kernel": "k_fused_pass",
+                         "peak_kind": peak_kind, "kernel": "k_fused_herm",
                          "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (4 ** nq),

@@ -95,6 +95,7 @@ QCW_API qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k);
 #define QCW_FUSED_KERNEL_PIPE 2
 #define QCW_FUSED_KERNEL_HERM 3
 #define QCW_FUSED_KERNEL_HERMC 4 /* HERM with the superoperators read from the constant bank */
+#define QCW_FUSED_KERNEL_HERMP 5 /* HERM on persistent double-buffered CTAs */
 QCW_API qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which);
 
 /* Device pointer of rho and the context's stream (borrowed; valid until destroy). */

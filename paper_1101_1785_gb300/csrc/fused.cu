@@ -203,6 +203,27 @@ __device__ __forceinline__ void pair_of(unsigned p, unsigned &o_r, unsigned &o_c
 
 constexpr int HT = 128;  // threads of the Hermitian kernel: 2^12-element tiles give 2 groups each
 
+// Mirror tile: element t' holds conj(tile[swap(t')]), swap exchanging the column half and the
+// row half of the tile index.  Adjacent lanes take adjacent elements of one contiguous run
+// (up to 32-byte segments) and walk the tile's rows in the other lane bits, so that the
+// shared-memory reads spread over the banks.
+template <int NT>
+__device__ __forceinline__ void herm_mirror(float2 *__restrict__ rho, const FPass &P, uint64_t mbase,
+                                            const float2 *__restrict__ tile, const uint64_t *__restrict__ hoff)
+{
+    const int TB = P.TB, L = P.L, h = P.TB / 2;
+    const int J = L < 2 ? L : 2;
+    const unsigned hmask = (1u << h) - 1u, lmask = (1u << L) - 1u, jmask = (1u << J) - 1u;
+    for (unsigned idx = threadIdx.x; idx < (1u << TB); idx += NT) {
+        const unsigned j = idx & jmask, u = idx >> J;
+        const unsigned Rp = u & hmask, Chi = u >> h;
+        const unsigned tp = (Rp << h) | (Chi << J) | j;
+        const unsigned ts = (((Chi << J) | j) << h) | Rp;
+        const float2 v = tile[ts];
+        rho[mbase + hoff[tp >> L] + (tp & lmask)] = make_float2(v.x, -v.y);
+    }
+}
+
 __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, const FPass *__restrict__ passes,
                                                       const FPhase *__restrict__ phases,
                                                       const float2 *__restrict__ coefs, int pass_idx)
@@ -232,26 +253,70 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
         const int ncoef = phase_coefs(F.nq);
         for (int i = threadIdx.x; i < ncoef; i += HT) sm.S[i] = coefs[F.coef + i];
         __syncthreads();
-        tile_apply_phase<HT>(sm.tile, TB, F, sm.S);
+        tile_apply_phase<HT, false>(sm.tile, TB, F, sm.S);
         __syncthreads();
     }
     tile_store_nt<HT>(rho, P, t_self, sm.tile, sm.hoff);
     if (o_r == o_c) return;
-    // mirror tile: element t' holds conj(tile[swap(t')]), swap exchanging the column half and
-    // the row half of the tile index.  Adjacent lanes take adjacent elements of one contiguous
-    // run (32-byte segments) and walk the tile's rows in the other lane bits, so that the
-    // shared-memory reads spread over the banks.
-    const uint64_t mbase = tile_base(P, ((uint64_t)o_c << m) | o_r);
-    const int J = L < 2 ? L : 2;
-    const unsigned hmask = (1u << h) - 1u, lmask = (1u << L) - 1u, jmask = (1u << J) - 1u;
-    for (unsigned idx = threadIdx.x; idx < (1u << TB); idx += HT) {
-        const unsigned j = idx & jmask, u = idx >> J;
-        const unsigned Rp = u & hmask, Chi = u >> h;
-        const unsigned tp = (Rp << h) | (Chi << J) | j;
-        const unsigned ts = (((Chi << J) | j) << h) | Rp;
-        const float2 v = sm.tile[ts];
-        rho[mbase + sm.hoff[tp >> L] + (tp & lmask)] = make_float2(v.x, -v.y);
+    herm_mirror<HT>(rho, P, tile_base(P, ((uint64_t)o_c << m) | o_r), sm.tile, sm.hoff);
+}
+
+// Persistent double-buffered Hermitian pass: each CTA walks the pairs blockIdx.x,
+// blockIdx.x + gridDim.x, ... and prefetches the next pair's tile with cp.async while it
+// evolves the current one, so that its HBM traffic overlaps its arithmetic.
+static size_t hermp_smem_bytes(int TB, int L)
+{
+    return 2 * ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + 256 * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(HT, 2) k_fused_hermp(float2 *__restrict__ rho, const FPass *__restrict__ passes,
+                                                       const FPhase *__restrict__ phases,
+                                                       const float2 *__restrict__ coefs, int pass_idx, unsigned npairs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const FPass &P = passes[pass_idx];
+    const int TB = P.TB, L = P.L, m = P.nother / 2;
+    float2 *buf0 = reinterpret_cast<float2 *>(smem);
+    float2 *buf1 = buf0 + (1u << TB);
+    uint64_t *hoff = reinterpret_cast<uint64_t *>(buf1 + (1u << TB));
+    float2 *S = reinterpret_cast<float2 *>(hoff + ((1u << (TB - L)) | 1u) + 1u);
+    tile_hoff_nt<HT>(P, hoff);
+    __syncthreads();
+    const unsigned nvec = 1u << (TB - 1), lmask = (1u << L) - 1u;
+    auto issue = [&](unsigned pr, float2 *buf) {
+        unsigned a, b;
+        pair_of(pr, a, b);
+        const uint64_t base = tile_base(P, ((uint64_t)a << m) | b);
+        for (unsigned v = threadIdx.x; v < nvec; v += HT) {
+            unsigned e = 2 * v;
+            cp_async16(&buf[e], rho + base + hoff[e >> L] + (e & lmask));
+        }
+    };
+    unsigned p = blockIdx.x;
+    if (p < npairs) issue(p, buf0);
+    cp_async_commit();
+    for (unsigned j = 0; p < npairs; j++, p += gridDim.x) {
+        float2 *cur = (j & 1) ? buf1 : buf0;
+        float2 *nxt = (j & 1) ? buf0 : buf1;
+        if (p + gridDim.x < npairs) issue(p + gridDim.x, nxt);
+        cp_async_commit();
+        cp_async_wait_group1();
+        __syncthreads();
+        for (int ph = 0; ph < P.nphase; ph++) {
+            const FPhase F = phases[P.phase0 + ph];
+            const int ncoef = phase_coefs(F.nq);
+            for (int i = threadIdx.x; i < ncoef; i += HT) S[i] = coefs[F.coef + i];
+            __syncthreads();
+            tile_apply_phase<HT, false>(cur, TB, F, S);
+            __syncthreads();
+        }
+        unsigned o_r, o_c;
+        pair_of(p, o_r, o_c);
+        tile_store_nt<HT>(rho, P, ((uint64_t)o_r << m) | o_c, cur, hoff);
+        if (o_r != o_c) herm_mirror<HT>(rho, P, tile_base(P, ((uint64_t)o_c << m) | o_r), cur, hoff);
+        __syncthreads();
     }
+    cp_async_wait_all();
 }
 
 // Same Hermitian pass with the pass's phase headers and superoperators carried in the kernel
@@ -338,7 +403,7 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
     const int n = c->n;
     TilePlan tp;
     const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
-                      c->fused_kernel == QCW_FUSED_KERNEL_HERMC;
+                      c->fused_kernel == QCW_FUSED_KERNEL_HERMC || c->fused_kernel == QCW_FUSED_KERNEL_HERMP;
     append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp, herm);
     cp.hpass = tp.passes;
     cp.smem = tp.smem;
@@ -402,7 +467,37 @@ static void release_plan(CachedPlan &cp)
     cp.dbuf = nullptr;
 }
 
-static int auto_k(int n) { return n < 5 ? n : 5; }
+// Fusion width for the fused path: the candidate with the lowest modeled time.  The model
+// is fitted to GB300 measurements of the Hermitian pass kernel on the 14-qubit benchmark
+// circuit: a pass costs its HBM round trip, whose speed depends on the length of the tiles'
+// contiguous runs (16-byte runs reach ~3.6 TB/s, 32-byte runs ~5 TB/s, longer ~5.7 TB/s),
+// plus ~1.05 ps per element for each two-qubit phase (a quarter of that for one-qubit and
+// half for product phases).  Both fits reproduce the measured steps within 3 %.
+static double fused_cost(const TilePlan &tp, int n)
+{
+    const double el = (double)(1ull << (2 * n));
+    double c = 0;
+    for (const FPass &p : tp.passes) c += el * (p.L <= 1 ? 3.35e-12 : p.L == 2 ? 2.4e-12 : 2.2e-12);
+    for (const FPhase &f : tp.phases) c += el * (f.nq == PH_TWO ? 1.05e-12 : f.nq == PH_PRODUCT ? 0.55e-12 : 0.3e-12);
+    return c;
+}
+
+static int auto_k(const std::vector<QOp> &ops, size_t b, size_t e, int n, bool herm, int tbmax)
+{
+    if (n <= 3) return n;
+    int best = 4;
+    double bc = -1;
+    for (int k = 3; k <= 5 && k <= n; k++) {
+        TilePlan tp;
+        append_tile_plan(plan_passes(ops, b, e, n, k, true), n, tbmax, tp, herm);
+        const double c = fused_cost(tp, n);
+        if (bc < 0 || c < bc) {
+            bc = c;
+            best = k;
+        }
+    }
+    return best;
+}
 
 static const size_t kMaxCached = 64;
 
@@ -410,10 +505,12 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
 {
     FusedRuntime *rt = c->fused;
     const int n = c->n;
-    int k = c->fuse_k ? c->fuse_k : auto_k(n);
+    const bool herm0 = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
+                       c->fused_kernel == QCW_FUSED_KERNEL_HERMC || c->fused_kernel == QCW_FUSED_KERNEL_HERMP;
+    int k = c->fuse_k ? c->fuse_k : auto_k(c->queue, b, e, n, herm0, herm0 ? 12 : 13);
     if (k > n) k = n;
     const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
-                      c->fused_kernel == QCW_FUSED_KERNEL_HERMC;
+                      c->fused_kernel == QCW_FUSED_KERNEL_HERMC || c->fused_kernel == QCW_FUSED_KERNEL_HERMP;
     const int tbmax = herm ? 12 : 13;
     uint64_t h = hash_ops(c->queue, b, e, n, k, tbmax) ^ (0x9e3779b97f4a7c15ull * (uint64_t)(c->fused_kernel + 1));
     CachedPlan *hit = nullptr;
@@ -456,6 +553,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm), maxsm);
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm_c), maxsm);
+    if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_hermp), hermp_smem_bytes(12, 1));
     if (!sst && maxpipe) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pipe), maxpipe);
     if (sst) return sst;
     const FPass *dp = reinterpret_cast<const FPass *>(hit->dbuf);
@@ -475,6 +573,10 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
         }
         if (hit->hpass[p].herm && hit->param_idx[p] >= 0 && c->fused_kernel == QCW_FUSED_KERNEL_HERMC) {
             k_fused_herm_c<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, hit->params[hit->param_idx[p]]);
+        } else if (hit->hpass[p].herm && c->fused_kernel == QCW_FUSED_KERNEL_HERMP && hit->grid[p] >= 8 * c->nsm) {
+            const FPass &fp = hit->hpass[p];
+            k_fused_hermp<<<2 * c->nsm, HT, hermp_smem_bytes(fp.TB, fp.L), c->stream>>>(c->rho, dp, dph, dco, (int)p,
+                                                                                      (unsigned)hit->grid[p]);
         } else if (hit->hpass[p].herm) {
             k_fused_herm<<<hit->grid[p], HT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
         } else if (hit->pipe[p]) {

@@ -23,6 +23,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// 16-byte shared-memory load that the compiler may neither hoist nor merge.
+__device__ __forceinline__ float4 lds_v4_volatile(const float4 *p)
+{
+    float4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ unsigned ins0u(unsigned x, int p)
 {
     unsigned lo = x & ((1u << p) - 1u);
@@ -31,7 +40,7 @@ __device__ __forceinline__ unsigned ins0u(unsigned x, int p)
 
 // Two-qubit phase: 16x16 superoperator S (shared memory, row-major) on every group.
 // G groups per thread share each coefficient load.
-template <int G, int NT = kTileThreads>
+template <int G, int NT = kTileThreads, bool UNROLL = true>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
 {
@@ -56,19 +65,20 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
                 x[j][e] = tile[base[j] + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) +
                                ((e & 1) ? d3 : 0u)];
         }
-        // The member loop stays rolled so that the 256 coefficients are re-read from shared
-        // memory (broadcast) instead of being hoisted into registers.
-#pragma unroll 1
+        // Member loop: fully unrolled (UNROLL) the member offsets are compile-time sums of
+        // d0..d3; rolled it needs fewer registers.  The coefficient reads are volatile
+        // shared-memory loads so that the compiler re-reads them (a broadcast per warp)
+        // instead of hoisting all 256 into registers.
+#pragma unroll(UNROLL ? 16 : 1)
         for (int e = 0; e < 16; e++) {
             const unsigned oe = ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u);
-            // two partial sums per output (even / odd inputs) halve the dependent FMA chain
             float2 y0[G], y1[G];
 #pragma unroll
             for (int j = 0; j < G; j++) y0[j] = y1[j] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int f = 0; f < 16; f += 2) {
-                float4 c = S4[8 * e + (f >> 1)];
-                float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
+                const float4 c = lds_v4_volatile(S4 + 8 * e + (f >> 1));
+                const float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
 #pragma unroll
                 for (int j = 0; j < G; j++) {
                     cfma(y0[j], c0, x[j][f]);
@@ -172,14 +182,14 @@ __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int T
 }
 
 // Apply one phase whose coefficients are at S (shared or global memory).
-template <int NT = kTileThreads>
+template <int NT = kTileThreads, bool UNROLL = true>
 __device__ __forceinline__ void tile_apply_phase(float2 *__restrict__ tile, int TB, const FPhase &F,
                                                  const float2 *__restrict__ S)
 {
     if (F.nq == PH_TWO) {
         constexpr int kLogNT = NT == 128 ? 7 : NT == 256 ? 8 : NT == 512 ? 9 : 10;
-        if (TB - 4 >= kLogNT + 1) tile_phase2<2, NT>(tile, TB, F, S);  // >= 2 groups per thread
-        else tile_phase2<1, NT>(tile, TB, F, S);
+        if (TB - 4 >= kLogNT + 1) tile_phase2<2, NT, UNROLL>(tile, TB, F, S);  // >= 2 groups per thread
+        else tile_phase2<1, NT, UNROLL>(tile, TB, F, S);
     } else if (F.nq == PH_PRODUCT) {
         tile_phase_prod<NT>(tile, TB, F, S);
     } else {
