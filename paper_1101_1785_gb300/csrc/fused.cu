@@ -62,11 +62,44 @@ struct CachedPlan {
     long long last_use = 0;
 };
 
+// Measured choice of the fusion width (fuse_k = 0): the first segments of at least
+// kTuneMinOps operations run with each candidate width in turn, timed with events; once all
+// candidates have a time per operation the fastest is kept for the context's lifetime.
+constexpr int kTuneCand[2] = {4, 5};
+constexpr size_t kTuneMinOps = 64;
+
+struct KTune {
+    int stage = 0;           // candidates measured so far
+    int chosen = 0;          // 0 until decided
+    double ms_per_op[2] = {0, 0};
+    bool pending = false;    // a timed trial is in flight
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    size_t nops = 0;
+};
+
 struct FusedRuntime {
     std::vector<CachedPlan> cache;
     long long tick = 0;
     std::vector<cudaEvent_t> ev_free, ev_pending;  // pairs: start, stop
+    KTune tune;
 };
+
+// Collect a finished trial; returns true while the trial is still running.
+static bool tune_poll(KTune &t)
+{
+    if (!t.pending) return false;
+    if (cudaEventQuery(t.e1) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess && t.nops) t.ms_per_op[t.stage] = ms / (double)t.nops;
+    cudaGetLastError();
+    t.pending = false;
+    t.stage++;
+    if (t.stage == 2) t.chosen = t.ms_per_op[0] <= t.ms_per_op[1] ? kTuneCand[0] : kTuneCand[1];
+    return false;
+}
 
 static uint64_t fnv(uint64_t h, const void *p, size_t n)
 {
@@ -233,10 +266,12 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
     const int TB = P.TB, L = P.L, h = P.TB / 2, m = P.nother / 2;
     const TileSmem sm = tile_smem(smem, TB, L);
     tile_hoff_nt<HT>(P, sm.hoff);
+    // The evolved tile is the one with o_c <= o_r (on or below the diagonal): consecutive CTAs
+    // then differ in the outside column bits, so tiles running side by side read adjacent
+    // contiguous runs of rho.  Outside bits ascend: m column bits (o_c) below m row bits (o_r).
     unsigned o_r, o_c;
-    pair_of(blockIdx.x, o_r, o_c);
+    pair_of(blockIdx.x, o_c, o_r);
     __syncthreads();
-    // outside bits ascend: m column bits (o_c) below m row bits (o_r)
     const uint64_t t_self = ((uint64_t)o_r << m) | o_c;
     {
         const uint64_t base = tile_base(P, t_self);
@@ -507,7 +542,19 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     const int n = c->n;
     const bool herm0 = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
                        c->fused_kernel == QCW_FUSED_KERNEL_HERMC || c->fused_kernel == QCW_FUSED_KERNEL_HERMP;
-    int k = c->fuse_k ? c->fuse_k : auto_k(c->queue, b, e, n, herm0, herm0 ? 12 : 13);
+    KTune &tn = rt->tune;
+    bool trial = false;
+    int k;
+    if (c->fuse_k) {
+        k = c->fuse_k;
+    } else if (tn.chosen) {
+        k = tn.chosen;
+    } else if (n >= 12 && herm0 && e - b >= kTuneMinOps && !tune_poll(tn) && !tn.chosen) {
+        k = kTuneCand[tn.stage];
+        trial = true;
+    } else {
+        k = tn.chosen ? tn.chosen : auto_k(c->queue, b, e, n, herm0, herm0 ? 12 : 13);
+    }
     if (k > n) k = n;
     const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
                       c->fused_kernel == QCW_FUSED_KERNEL_HERMC || c->fused_kernel == QCW_FUSED_KERNEL_HERMP;
@@ -556,6 +603,13 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_hermp), hermp_smem_bytes(12, 1));
     if (!sst && maxpipe) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pipe), maxpipe);
     if (sst) return sst;
+    if (trial) {
+        if (!tn.e0) {
+            cudaEventCreate(&tn.e0);
+            cudaEventCreate(&tn.e1);
+        }
+        cudaEventRecord(tn.e0, c->stream);
+    }
     const FPass *dp = reinterpret_cast<const FPass *>(hit->dbuf);
     const FPhase *dph = reinterpret_cast<const FPhase *>(hit->dbuf + hit->phase_off);
     const float2 *dco = reinterpret_cast<const float2 *>(hit->dbuf + hit->coef_off);
@@ -595,6 +649,11 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
         }
         cudaError_t er = cudaGetLastError();
         if (er != cudaSuccess) return cuda_error(er, "fused pass launch");
+    }
+    if (trial) {
+        cudaEventRecord(tn.e1, c->stream);
+        tn.nops = e - b;
+        tn.pending = true;
     }
     return QCW_OK;
 }
@@ -665,6 +724,8 @@ void fused_destroy(qcw_ctx *c)
     for (CachedPlan &cp : rt->cache) release_plan(cp);
     for (cudaEvent_t e : rt->ev_free) cudaEventDestroy(e);
     for (cudaEvent_t e : rt->ev_pending) cudaEventDestroy(e);
+    if (rt->tune.e0) cudaEventDestroy(rt->tune.e0);
+    if (rt->tune.e1) cudaEventDestroy(rt->tune.e1);
     delete rt;
     c->fused = nullptr;
 }
