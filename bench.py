@@ -51,7 +51,7 @@ def parse_args():
                          "one launch; serve: Poisson request stream through the continuous-batching server")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
-    ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "pipe", "herm", "hermc", "hermp"],
+    ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "herm"],
                     help="kernel for large fused passes (results are identical)")
     ap.add_argument("--fuse-k", type=int, default=FUSE_K, help="qubits per fused pass")
     ap.add_argument("--qubits", type=int, default=N_QUBITS,
@@ -256,7 +256,7 @@ def run_ours(args):
     packed = [q.PackedOps(p) for p in parts]
     d = q.Density(nq)
     d.set_mode(q.QCW_MODE_FUSED, args.fuse_k)
-    d.set_fused_kernel({"auto": 0, "tile": 1, "pipe": 2, "herm": 3, "hermc": 4, "hermp": 5}[args.fused_kernel])
+    d.set_fused_kernel({"auto": 0, "tile": 1, "herm": 2}[args.fused_kernel])
     rho_ptr, stream_ptr = d.device_state()
     ext = torch.cuda.ExternalStream(stream_ptr)
 

@@ -85,17 +85,13 @@ QCW_API qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k);
 /* Which kernel runs fused passes.
  *   HERM (and AUTO, the default): rho is a density matrix, hence Hermitian (Sec. 5.2, rho^dagger
  *     = rho).  Tiles hold the row and column bits of the same qubits; each pass evolves the
- *     tiles on or above the diagonal and writes the others as their conjugate transposes (half
- *     the arithmetic).  A non-Hermitian matrix loaded with qcw_set_state is not preserved.
+ *     tiles on one side of the diagonal and writes the others as their conjugate transposes
+ *     (half the arithmetic).  A non-Hermitian matrix loaded with qcw_set_state is not preserved.
  *   TILE: one CTA per tile, no symmetry assumed.
- *   PIPE: persistent double-buffered CTAs, no symmetry assumed.
  * Flushes queued work first. */
 #define QCW_FUSED_KERNEL_AUTO 0
 #define QCW_FUSED_KERNEL_TILE 1
-#define QCW_FUSED_KERNEL_PIPE 2
-#define QCW_FUSED_KERNEL_HERM 3
-#define QCW_FUSED_KERNEL_HERMC 4 /* HERM with the superoperators read from the constant bank */
-#define QCW_FUSED_KERNEL_HERMP 5 /* HERM on persistent double-buffered CTAs */
+#define QCW_FUSED_KERNEL_HERM 2
 QCW_API qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which);
 
 /* Device pointer of rho and the context's stream (borrowed; valid until destroy). */

@@ -206,7 +206,7 @@ class Density:
         check(lib().qcw_set_mode(self.h, int(mode), int(fuse_k)), "qcw_set_mode")
 
     def set_fused_kernel(self, which: int):
-        """0 = auto (Hermitian), 1 = one CTA per tile, 2 = persistent double-buffered, 3 = Hermitian."""
+        """0 = auto (Hermitian), 1 = one CTA per tile (no symmetry assumed), 2 = Hermitian."""
         check(lib().qcw_set_fused_kernel(self.h, int(which)), "qcw_set_fused_kernel")
 
     def device_state(self):

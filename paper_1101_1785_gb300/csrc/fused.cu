@@ -21,17 +21,6 @@ namespace qcw {
 
 constexpr int FT = kTileThreads;
 
-// Parameter block of the Hermitian kernel that reads its superoperators from the constant bank.
-constexpr int kParamPhaseMax = 24;
-constexpr int kParamCoefMax = 3520;  // float2: the whole block stays under the 32 KiB limit
-
-struct PassParams {
-    FPass pass;
-    FPhase phases[kParamPhaseMax];
-    float2 coefs[kParamCoefMax];
-};
-
-
 // One CTA per tile of one pass.
 __global__ void __launch_bounds__(FT, 2) k_fused_pass(float2 *__restrict__ rho, const FPass *__restrict__ passes,
                                                    const FPhase *__restrict__ phases, const float2 *__restrict__ coefs,
@@ -53,10 +42,6 @@ struct CachedPlan {
     std::vector<FPass> hpass;
     std::vector<int> grid;  // tiles per pass
     std::vector<size_t> smem;
-    std::vector<char> pipe;  // pass runs on the persistent double-buffered kernel
-    std::vector<size_t> pipe_smem;
-    std::vector<PassParams> params;  // Hermitian passes whose superoperators fit the parameter block
-    std::vector<int> param_idx;      // index into params, or -1
     char *dbuf = nullptr;  // device copy of passes | phases | coefs
     size_t phase_off = 0, coef_off = 0;
     long long last_use = 0;
@@ -138,85 +123,6 @@ static bool same_ops(const std::vector<QOp> &a, const std::vector<QOp> &ops, siz
     return true;
 }
 
-// Persistent, double-buffered form: one CTA of kPipeThreads per SM walks tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...; while it applies the phases to tile j (all the
-// pass's superoperators are staged in shared memory once), the cp.async copy of tile j+1 is
-// already in flight, so the HBM traffic overlaps the FP32 work.
-constexpr int kPipeThreads = 256;
-constexpr int kPipeCoefMax = 24 * 256;  // staged coefficients (24 two-qubit phases, 48 KiB)
-constexpr int kPipePhaseMax = 64;
-
-static size_t pipe_smem_bytes(int TB, int L)
-{
-    return 2 * ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + sizeof(float2) * kPipeCoefMax +
-           sizeof(FPhase) * kPipePhaseMax;
-}
-
-__device__ __forceinline__ void pipe_issue(const float2 *__restrict__ rho, const FPass &P, uint64_t t,
-                                           float2 *__restrict__ buf, const uint64_t *__restrict__ hoff)
-{
-    const int TB = P.TB, L = P.L;
-    const uint64_t base = tile_base(P, t);
-    const unsigned nvec = 1u << (TB - 1);
-    const unsigned lmask = (1u << L) - 1u;
-    for (unsigned v = threadIdx.x; v < nvec; v += kPipeThreads) {
-        unsigned e = 2 * v;
-        cp_async16(&buf[e], rho + base + hoff[e >> L] + (e & lmask));
-    }
-}
-
-__global__ void __launch_bounds__(kPipeThreads, 1) k_fused_pipe(float2 *__restrict__ rho, const FPass *__restrict__ passes,
-                                                                const FPhase *__restrict__ phases,
-                                                                const float2 *__restrict__ coefs, int pass_idx,
-                                                                unsigned ntiles)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const FPass &P = passes[pass_idx];
-    const int TB = P.TB, L = P.L;
-    float2 *buf0 = reinterpret_cast<float2 *>(smem);
-    float2 *buf1 = buf0 + (1u << TB);
-    uint64_t *hoff = reinterpret_cast<uint64_t *>(buf1 + (1u << TB));
-    float2 *S = reinterpret_cast<float2 *>(hoff + ((1u << (TB - L)) | 1u) + 1u);
-    FPhase *F = reinterpret_cast<FPhase *>(S + kPipeCoefMax);
-    tile_hoff_nt<kPipeThreads>(P, hoff);
-    // stage the pass's phase headers and coefficients (offsets rebased to the staged copy)
-    const int nph = P.nphase;
-    const int c0 = nph ? phases[P.phase0].coef : 0;
-    int ncoef = 0;
-    if (nph) {
-        const FPhase &last = phases[P.phase0 + nph - 1];
-        ncoef = last.coef + phase_coefs(last.nq) - c0;
-    }
-    for (int i = threadIdx.x; i < nph; i += kPipeThreads) {
-        FPhase f = phases[P.phase0 + i];
-        f.coef -= c0;
-        F[i] = f;
-    }
-    for (int i = threadIdx.x; i < ncoef; i += kPipeThreads) S[i] = coefs[c0 + i];
-    __syncthreads();
-
-    unsigned t = blockIdx.x;
-    if (t < ntiles) pipe_issue(rho, P, t, buf0, hoff);
-    cp_async_commit();
-    for (unsigned j = 0; t < ntiles; j++, t += gridDim.x) {
-        float2 *cur = (j & 1) ? buf1 : buf0;
-        float2 *nxt = (j & 1) ? buf0 : buf1;
-        const unsigned tn = t + gridDim.x;
-        if (tn < ntiles) pipe_issue(rho, P, tn, nxt, hoff);
-        cp_async_commit();
-        cp_async_wait_group1();  // everything but the newest group: tile t has landed
-        __syncthreads();
-        for (int ph = 0; ph < nph; ph++) {
-            const FPhase f = F[ph];
-            tile_apply_phase<kPipeThreads>(cur, TB, f, S + f.coef);
-            __syncthreads();
-        }
-        tile_store_nt<kPipeThreads>(rho, P, t, cur, hoff);
-        __syncthreads();  // cur is refilled two iterations later
-    }
-    cp_async_wait_all();
-}
-
 // Hermitian form (rho = rho^dagger, Sec. 5.2): tiles are symmetric (row and column bits of
 // the same qubits), so the conjugate transpose of the tile with outside bits (o_r, o_c) is
 // the tile (o_c, o_r) and the pass maps it to the conjugate transpose of its own image.  One
@@ -296,140 +202,9 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
     herm_mirror<HT>(rho, P, tile_base(P, ((uint64_t)o_c << m) | o_r), sm.tile, sm.hoff);
 }
 
-// Persistent double-buffered Hermitian pass: each CTA walks the pairs blockIdx.x,
-// blockIdx.x + gridDim.x, ... and prefetches the next pair's tile with cp.async while it
-// evolves the current one, so that its HBM traffic overlaps its arithmetic.
-static size_t hermp_smem_bytes(int TB, int L)
+static bool herm_kernel(const qcw_ctx *c)
 {
-    return 2 * ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + 256 * sizeof(float2);
-}
-
-__global__ void __launch_bounds__(HT, 2) k_fused_hermp(float2 *__restrict__ rho, const FPass *__restrict__ passes,
-                                                       const FPhase *__restrict__ phases,
-                                                       const float2 *__restrict__ coefs, int pass_idx, unsigned npairs)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const FPass &P = passes[pass_idx];
-    const int TB = P.TB, L = P.L, m = P.nother / 2;
-    float2 *buf0 = reinterpret_cast<float2 *>(smem);
-    float2 *buf1 = buf0 + (1u << TB);
-    uint64_t *hoff = reinterpret_cast<uint64_t *>(buf1 + (1u << TB));
-    float2 *S = reinterpret_cast<float2 *>(hoff + ((1u << (TB - L)) | 1u) + 1u);
-    tile_hoff_nt<HT>(P, hoff);
-    __syncthreads();
-    const unsigned nvec = 1u << (TB - 1), lmask = (1u << L) - 1u;
-    auto issue = [&](unsigned pr, float2 *buf) {
-        unsigned a, b;
-        pair_of(pr, a, b);
-        const uint64_t base = tile_base(P, ((uint64_t)a << m) | b);
-        for (unsigned v = threadIdx.x; v < nvec; v += HT) {
-            unsigned e = 2 * v;
-            cp_async16(&buf[e], rho + base + hoff[e >> L] + (e & lmask));
-        }
-    };
-    unsigned p = blockIdx.x;
-    if (p < npairs) issue(p, buf0);
-    cp_async_commit();
-    for (unsigned j = 0; p < npairs; j++, p += gridDim.x) {
-        float2 *cur = (j & 1) ? buf1 : buf0;
-        float2 *nxt = (j & 1) ? buf0 : buf1;
-        if (p + gridDim.x < npairs) issue(p + gridDim.x, nxt);
-        cp_async_commit();
-        cp_async_wait_group1();
-        __syncthreads();
-        for (int ph = 0; ph < P.nphase; ph++) {
-            const FPhase F = phases[P.phase0 + ph];
-            const int ncoef = phase_coefs(F.nq);
-            for (int i = threadIdx.x; i < ncoef; i += HT) S[i] = coefs[F.coef + i];
-            __syncthreads();
-            tile_apply_phase<HT, false>(cur, TB, F, S);
-            __syncthreads();
-        }
-        unsigned o_r, o_c;
-        pair_of(p, o_r, o_c);
-        tile_store_nt<HT>(rho, P, ((uint64_t)o_r << m) | o_c, cur, hoff);
-        if (o_r != o_c) herm_mirror<HT>(rho, P, tile_base(P, ((uint64_t)o_c << m) | o_r), cur, hoff);
-        __syncthreads();
-    }
-    cp_async_wait_all();
-}
-
-// Same Hermitian pass with the pass's phase headers and superoperators carried in the kernel
-// parameter block (constant bank): every thread reads the same coefficient at the same time,
-// so the reads go through the constant cache instead of competing with the tile's
-// shared-memory traffic.
-__device__ __forceinline__ void cphase2(float2 *__restrict__ tile, int TB, const FPhase &F, const PassParams &pp)
-{
-    const unsigned d0 = 1u << F.pos[0], d1 = 1u << F.pos[1], d2 = 1u << F.pos[2], d3 = 1u << F.pos[3];
-    int p[4] = {F.pos[0], F.pos[1], F.pos[2], F.pos[3]};
-#pragma unroll
-    for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int b = a + 1; b < 4; b++)
-            if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
-    const unsigned ng = 1u << (TB - 4);
-    for (unsigned g = threadIdx.x; g < ng; g += FT) {
-        const unsigned base = ins0u(ins0u(ins0u(ins0u(g, p[0]), p[1]), p[2]), p[3]);
-        float2 x[16];
-#pragma unroll
-        for (int e = 0; e < 16; e++)
-            x[e] = tile[base + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u)];
-#pragma unroll 2
-        for (int e = 0; e < 16; e++) {
-            const unsigned oe = ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u);
-            const float2 *row = pp.coefs + F.coef + 16 * e;
-            float2 y0 = make_float2(0.f, 0.f), y1 = y0;
-#pragma unroll
-            for (int f = 0; f < 16; f += 2) {
-                cfma(y0, row[f], x[f]);
-                cfma(y1, row[f + 1], x[f + 1]);
-            }
-            tile[base + oe] = cadd(y0, y1);
-        }
-    }
-}
-
-__device__ __forceinline__ void cphase_small(float2 *__restrict__ tile, int TB, const FPhase &F, const PassParams &pp)
-{
-    float2 s[32];
-    const int nc = F.nq == PH_PRODUCT ? 32 : 16;
-#pragma unroll
-    for (int i = 0; i < 32; i++) s[i] = i < nc ? pp.coefs[F.coef + i] : make_float2(0.f, 0.f);
-    if (F.nq == PH_PRODUCT) tile_phase_prod<FT>(tile, TB, F, s);
-    else tile_phase1<FT>(tile, TB, F, s);
-}
-
-__global__ void __launch_bounds__(FT, 2) k_fused_herm_c(float2 *__restrict__ rho, const __grid_constant__ PassParams pp)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const FPass &P = pp.pass;
-    const int TB = P.TB, L = P.L, h = P.TB / 2, m = P.nother / 2;
-    const TileSmem sm = tile_smem(smem, TB, L);
-    tile_hoff(P, sm.hoff);
-    unsigned o_r, o_c;
-    pair_of(blockIdx.x, o_r, o_c);
-    __syncthreads();
-    const uint64_t t_self = ((uint64_t)o_r << m) | o_c;
-    tile_load(rho, P, t_self, sm, false);
-    for (int ph = 0; ph < P.nphase; ph++) {
-        const FPhase F = pp.phases[ph];
-        if (F.nq == PH_TWO) cphase2(sm.tile, TB, F, pp);
-        else cphase_small(sm.tile, TB, F, pp);
-        __syncthreads();
-    }
-    tile_store(rho, P, t_self, sm);
-    if (o_r == o_c) return;
-    const uint64_t mbase = tile_base(P, ((uint64_t)o_c << m) | o_r);
-    const int J = L < 2 ? L : 2;
-    const unsigned hmask = (1u << h) - 1u, lmask = (1u << L) - 1u, jmask = (1u << J) - 1u;
-    for (unsigned idx = threadIdx.x; idx < (1u << TB); idx += FT) {
-        const unsigned j = idx & jmask, u = idx >> J;
-        const unsigned Rp = u & hmask, Chi = u >> h;
-        const unsigned tp = (Rp << h) | (Chi << J) | j;
-        const unsigned ts = (((Chi << J) | j) << h) | Rp;
-        const float2 v = sm.tile[ts];
-        rho[mbase + sm.hoff[tp >> L] + (tp & lmask)] = make_float2(v.x, -v.y);
-    }
+    return c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM;
 }
 
 static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, size_t e, int k, int tbmax,
@@ -437,44 +212,16 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
 {
     const int n = c->n;
     TilePlan tp;
-    const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
-                      c->fused_kernel == QCW_FUSED_KERNEL_HERMC || c->fused_kernel == QCW_FUSED_KERNEL_HERMP;
-    append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp, herm);
+    append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp, herm_kernel(c));
     cp.hpass = tp.passes;
     cp.smem = tp.smem;
     for (const FPass &fp : tp.passes) {
         if (fp.herm) {
             const unsigned long long M = 1ull << (fp.nother / 2);
             cp.grid.push_back((int)(M * (M + 1) / 2));
-            cp.pipe.push_back(0);
-            cp.pipe_smem.push_back(0);
-            int ncoef = 0;
-            for (int i = 0; i < fp.nphase; i++) ncoef += phase_coefs(tp.phases[fp.phase0 + i].nq);
-            if (fp.nphase <= kParamPhaseMax && ncoef <= kParamCoefMax) {
-                PassParams pp{};
-                pp.pass = fp;
-                const int c0 = fp.nphase ? tp.phases[fp.phase0].coef : 0;
-                for (int i = 0; i < fp.nphase; i++) {
-                    pp.phases[i] = tp.phases[fp.phase0 + i];
-                    pp.phases[i].coef -= c0;
-                }
-                for (int i = 0; i < ncoef; i++) pp.coefs[i] = tp.coefs[c0 + i];
-                cp.param_idx.push_back((int)cp.params.size());
-                cp.params.push_back(pp);
-            } else {
-                cp.param_idx.push_back(-1);
-            }
-            continue;
+        } else {
+            cp.grid.push_back(1 << fp.nother);
         }
-        cp.param_idx.push_back(-1);
-        cp.grid.push_back(1 << fp.nother);
-        int ncoef = 0;
-        for (int i = 0; i < fp.nphase; i++) ncoef += phase_coefs(tp.phases[fp.phase0 + i].nq);
-        const bool fits = fp.TB >= 12 && (1 << fp.nother) >= 4 * c->nsm && fp.nphase <= kPipePhaseMax &&
-                          ncoef <= kPipeCoefMax;
-        const bool ok = fits && c->fused_kernel == QCW_FUSED_KERNEL_PIPE;
-        cp.pipe.push_back(ok ? 1 : 0);
-        cp.pipe_smem.push_back(pipe_smem_bytes(fp.TB, fp.L));
     }
     size_t sz_pass = sizeof(FPass) * tp.passes.size();
     cp.phase_off = (sz_pass + 255) & ~(size_t)255;
@@ -540,8 +287,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
 {
     FusedRuntime *rt = c->fused;
     const int n = c->n;
-    const bool herm0 = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
-                       c->fused_kernel == QCW_FUSED_KERNEL_HERMC || c->fused_kernel == QCW_FUSED_KERNEL_HERMP;
+    const bool herm0 = herm_kernel(c);
     KTune &tn = rt->tune;
     bool trial = false;
     int k;
@@ -556,8 +302,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
         k = tn.chosen ? tn.chosen : auto_k(c->queue, b, e, n, herm0, herm0 ? 12 : 13);
     }
     if (k > n) k = n;
-    const bool herm = c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
-                      c->fused_kernel == QCW_FUSED_KERNEL_HERMC || c->fused_kernel == QCW_FUSED_KERNEL_HERMP;
+    const bool herm = herm0;
     const int tbmax = herm ? 12 : 13;
     uint64_t h = hash_ops(c->queue, b, e, n, k, tbmax) ^ (0x9e3779b97f4a7c15ull * (uint64_t)(c->fused_kernel + 1));
     CachedPlan *hit = nullptr;
@@ -592,16 +337,10 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     }
     hit->last_use = ++rt->tick;
 
-    size_t maxsm = 0, maxpipe = 0;
-    for (size_t p = 0; p < hit->smem.size(); p++) {
-        if (hit->pipe[p]) maxpipe = std::max(maxpipe, hit->pipe_smem[p]);
-        else maxsm = std::max(maxsm, hit->smem[p]);
-    }
+    size_t maxsm = 0;
+    for (size_t p = 0; p < hit->smem.size(); p++) maxsm = std::max(maxsm, hit->smem[p]);
     qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm), maxsm);
-    if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm_c), maxsm);
-    if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_hermp), hermp_smem_bytes(12, 1));
-    if (!sst && maxpipe) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pipe), maxpipe);
     if (sst) return sst;
     if (trial) {
         if (!tn.e0) {
@@ -625,18 +364,8 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             }
             cudaEventRecord(e0, c->stream);
         }
-        if (hit->hpass[p].herm && hit->param_idx[p] >= 0 && c->fused_kernel == QCW_FUSED_KERNEL_HERMC) {
-            k_fused_herm_c<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, hit->params[hit->param_idx[p]]);
-        } else if (hit->hpass[p].herm && c->fused_kernel == QCW_FUSED_KERNEL_HERMP && hit->grid[p] >= 8 * c->nsm) {
-            const FPass &fp = hit->hpass[p];
-            k_fused_hermp<<<2 * c->nsm, HT, hermp_smem_bytes(fp.TB, fp.L), c->stream>>>(c->rho, dp, dph, dco, (int)p,
-                                                                                      (unsigned)hit->grid[p]);
-        } else if (hit->hpass[p].herm) {
+        if (hit->hpass[p].herm) {
             k_fused_herm<<<hit->grid[p], HT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
-        } else if (hit->pipe[p]) {
-            const unsigned ntiles = (unsigned)hit->grid[p];
-            const unsigned g = std::min<unsigned>(ntiles, (unsigned)c->nsm);
-            k_fused_pipe<<<g, kPipeThreads, hit->pipe_smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p, ntiles);
         } else {
             k_fused_pass<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
         }

@@ -5,7 +5,7 @@ namespace qcw {
 
 size_t tile_smem_bytes(int TB, int L)
 {
-    return ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + 256 * sizeof(float2);
+    return ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + 512 * sizeof(float2);
 }
 
 // Tile bits of a pass: rows and columns of Q, then the lowest column bits until tbmax bits
@@ -67,7 +67,14 @@ void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TileP
                 f.pos[1] = (int8_t)tile_pos(fp, n - 1 - ph.qa);
                 out.nphase1++;
             }
-            for (const c128 &z : ph.S) out.coefs.push_back(make_float2((float)z.real(), (float)z.imag()));
+            if (f.nq == PH_TWO) {
+                for (const c128 &z : ph.S) {
+                    out.coefs.push_back(make_float2((float)z.real(), (float)z.real()));
+                    out.coefs.push_back(make_float2((float)z.imag(), (float)z.imag()));
+                }
+            } else {
+                for (const c128 &z : ph.S) out.coefs.push_back(make_float2((float)z.real(), (float)z.imag()));
+            }
             out.phases.push_back(f);
         }
         out.passes.push_back(fp);

@@ -23,14 +23,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// 16-byte shared-memory load that the compiler may neither hoist nor merge.
-__device__ __forceinline__ float4 lds_v4_volatile(const float4 *p)
-{
-    float4 v;
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-    return v;
-}
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ unsigned ins0u(unsigned x, int p)
 {
@@ -38,8 +31,40 @@ __device__ __forceinline__ unsigned ins0u(unsigned x, int p)
     return ((x ^ lo) << 1) | lo;
 }
 
-// Two-qubit phase: 16x16 superoperator S (shared memory, row-major) on every group.
-// G groups per thread share each coefficient load.
+// Packed FP32 (two lanes per register pair): d = a * b + c element-wise.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;\n" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;\n" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ float2 unpack2(unsigned long long v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;\n" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+// The two coefficient pairs (cr, cr), (ci, ci) of one expanded entry, at a 32-bit shared
+// address plus an immediate offset; volatile so that the compiler re-reads them (a broadcast
+// per warp) instead of hoisting a phase's 512 coefficient pairs into registers.
+template <int OFF>
+__device__ __forceinline__ void lds_coef(unsigned addr, unsigned long long &crr, unsigned long long &cii)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2+%3];\n" : "=l"(crr), "=l"(cii) : "r"(addr), "n"(OFF));
+}
+
+// Two-qubit phase on every 16-member group: y_e = sum_f S[e][f] x_f.  Each complex product is
+// two packed FMAs: (cr, cr) * (xr, xi) accumulates into P and (ci, ci) * (xr, xi) into Q, and
+// y = (P.re - Q.im, P.im + Q.re) at the end.  G groups per thread share each coefficient load.
 template <int G, int NT = kTileThreads, bool UNROLL = true>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
@@ -52,41 +77,54 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
         for (int b = a + 1; b < 4; b++)
             if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
     const unsigned ng = 1u << (TB - 4);
-    const float4 *S4 = reinterpret_cast<const float4 *>(S);
+    const unsigned sbase = smem_u32(S);
+    unsigned long long *t64 = reinterpret_cast<unsigned long long *>(tile);
     for (unsigned g0 = threadIdx.x; g0 < ng; g0 += G * NT) {
         unsigned base[G];
-        float2 x[G][16];
+        unsigned long long x[G][16];
 #pragma unroll
         for (int j = 0; j < G; j++) {
             unsigned g = g0 + j * NT;
             base[j] = ins0u(ins0u(ins0u(ins0u(g, p[0]), p[1]), p[2]), p[3]);
 #pragma unroll
             for (int e = 0; e < 16; e++)
-                x[j][e] = tile[base[j] + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) +
-                               ((e & 1) ? d3 : 0u)];
+                x[j][e] = t64[base[j] + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) +
+                              ((e & 1) ? d3 : 0u)];
         }
         // Member loop: fully unrolled (UNROLL) the member offsets are compile-time sums of
-        // d0..d3; rolled it needs fewer registers.  The coefficient reads are volatile
-        // shared-memory loads so that the compiler re-reads them (a broadcast per warp)
-        // instead of hoisting all 256 into registers.
+        // d0..d3; rolled it needs fewer registers.
 #pragma unroll(UNROLL ? 16 : 1)
         for (int e = 0; e < 16; e++) {
             const unsigned oe = ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u);
-            float2 y0[G], y1[G];
+            const unsigned se = sbase + 256u * (unsigned)e;  // row e: 16 entries x 16 bytes
+            unsigned long long P0[G], Q0[G], P1[G], Q1[G];
 #pragma unroll
-            for (int j = 0; j < G; j++) y0[j] = y1[j] = make_float2(0.f, 0.f);
+            for (int j = 0; j < G; j++) P0[j] = Q0[j] = P1[j] = Q1[j] = 0ull;
+#define QCW_PHASE2_STEP(F)                                                   \
+    {                                                                        \
+        unsigned long long crr, cii;                                         \
+        lds_coef<16 * (F)>(se, crr, cii);                                    \
+        _Pragma("unroll") for (int j = 0; j < G; j++)                        \
+        {                                                                    \
+            if ((F) & 1) {                                                   \
+                P1[j] = ffma2(crr, x[j][(F)], P1[j]);                        \
+                Q1[j] = ffma2(cii, x[j][(F)], Q1[j]);                        \
+            } else {                                                         \
+                P0[j] = ffma2(crr, x[j][(F)], P0[j]);                        \
+                Q0[j] = ffma2(cii, x[j][(F)], Q0[j]);                        \
+            }                                                                \
+        }                                                                    \
+    }
+            QCW_PHASE2_STEP(0) QCW_PHASE2_STEP(1) QCW_PHASE2_STEP(2) QCW_PHASE2_STEP(3)
+            QCW_PHASE2_STEP(4) QCW_PHASE2_STEP(5) QCW_PHASE2_STEP(6) QCW_PHASE2_STEP(7)
+            QCW_PHASE2_STEP(8) QCW_PHASE2_STEP(9) QCW_PHASE2_STEP(10) QCW_PHASE2_STEP(11)
+            QCW_PHASE2_STEP(12) QCW_PHASE2_STEP(13) QCW_PHASE2_STEP(14) QCW_PHASE2_STEP(15)
+#undef QCW_PHASE2_STEP
 #pragma unroll
-            for (int f = 0; f < 16; f += 2) {
-                const float4 c = lds_v4_volatile(S4 + 8 * e + (f >> 1));
-                const float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
-#pragma unroll
-                for (int j = 0; j < G; j++) {
-                    cfma(y0[j], c0, x[j][f]);
-                    cfma(y1[j], c1, x[j][f + 1]);
-                }
+            for (int j = 0; j < G; j++) {
+                const float2 P = unpack2(fadd2(P0[j], P1[j])), Q = unpack2(fadd2(Q0[j], Q1[j]));
+                tile[base[j] + oe] = make_float2(P.x - Q.y, P.y + Q.x);
             }
-#pragma unroll
-            for (int j = 0; j < G; j++) tile[base[j] + oe] = cadd(y0[j], y1[j]);
         }
     }
 }

@@ -204,7 +204,7 @@ def test_hermitian_kernel_matches_general_kernels(q, n):
     transposes) against the general per-tile kernel and, at n = 8, the oracle."""
     c = wl.random_circuit(n, 80, 808 + n, "mixed", "adpd")
     got = {}
-    for which in (1, 3):
+    for which in (1, 2):
         d = q.Density(n)
         d.set_mode(q.QCW_MODE_FUSED, 5)
         d.set_fused_kernel(which)
@@ -212,7 +212,24 @@ def test_hermitian_kernel_matches_general_kernels(q, n):
             d.apply_op(op)
         got[which] = d.get_state()
         d.close()
-    assert np.abs(got[3] - got[1]).max() <= 1e-6
-    assert np.abs(got[3] - got[3].conj().T).max() <= 1e-7
+    assert np.abs(got[2] - got[1]).max() <= 1e-6
+    assert np.abs(got[2] - got[2].conj().T).max() <= 1e-7
     if n == 8:
-        assert np.abs(got[3] - oracle.run_circuit(c)).max() <= ATOL
+        assert np.abs(got[2] - oracle.run_circuit(c)).max() <= ATOL
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_hermitian_kernel_at_n12(q, k):
+    """The Hermitian pass kernel at a size with thousands of tile pairs per pass, against the
+    general per-tile kernel."""
+    c = wl.random_circuit(12, 60, 1200 + k, "mixed", "adpd")
+    got = {}
+    for w in (1, 2):
+        d = q.Density(12)
+        d.set_mode(q.QCW_MODE_FUSED, k)
+        d.set_fused_kernel(w)
+        for op in c.ops:
+            d.apply_op(op)
+        got[w] = d.get_state()
+        d.close()
+    assert np.abs(got[2] - got[1]).max() <= 1e-6
