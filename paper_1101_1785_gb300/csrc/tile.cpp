@@ -5,7 +5,7 @@ namespace qcw {
 
 size_t tile_smem_bytes(int TB, int L)
 {
-    return ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + 512 * sizeof(float2);
+    return ((size_t)8 << TB) + 8 * ((((size_t)1 << (TB - L)) | 1) + 1) + 256 * sizeof(float2);
 }
 
 // Tile bits of a pass: rows and columns of Q, then the lowest column bits until tbmax bits
@@ -67,11 +67,15 @@ void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TileP
                 f.pos[1] = (int8_t)tile_pos(fp, n - 1 - ph.qa);
                 out.nphase1++;
             }
-            if (f.nq == PH_TWO) {
-                for (const c128 &z : ph.S) {
-                    out.coefs.push_back(make_float2((float)z.real(), (float)z.real()));
-                    out.coefs.push_back(make_float2((float)z.imag(), (float)z.imag()));
-                }
+            if (ph.S.empty()) {
+                // structure-only plan (width search): no coefficients
+            } else if (f.nq == PH_TWO) {
+                for (int in = 0; in < 16; in++)
+                    for (int pr = 0; pr < 8; pr++) {
+                        const c128 a = ph.S[(size_t)(2 * pr) * 16 + in], b = ph.S[(size_t)(2 * pr + 1) * 16 + in];
+                        out.coefs.push_back(make_float2((float)a.real(), (float)b.real()));
+                        out.coefs.push_back(make_float2((float)a.imag(), (float)b.imag()));
+                    }
             } else {
                 for (const c128 &z : ph.S) out.coefs.push_back(make_float2((float)z.real(), (float)z.imag()));
             }

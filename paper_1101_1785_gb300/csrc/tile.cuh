@@ -53,18 +53,28 @@ __device__ __forceinline__ float2 unpack2(unsigned long long v)
     return r;
 }
 
-// The two coefficient pairs (cr, cr), (ci, ci) of one expanded entry, at a 32-bit shared
-// address plus an immediate offset; volatile so that the compiler re-reads them (a broadcast
-// per warp) instead of hoisting a phase's 512 coefficient pairs into registers.
-template <int OFF>
-__device__ __forceinline__ void lds_coef(unsigned addr, unsigned long long &crr, unsigned long long &cii)
+__device__ __forceinline__ unsigned long long pack2(float a, float b)
 {
-    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2+%3];\n" : "=l"(crr), "=l"(cii) : "r"(addr), "n"(OFF));
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};\n" : "=l"(r) : "f"(a), "f"(b));
+    return r;
 }
 
-// Two-qubit phase on every 16-member group: y_e = sum_f S[e][f] x_f.  Each complex product is
-// two packed FMAs: (cr, cr) * (xr, xi) accumulates into P and (ci, ci) * (xr, xi) into Q, and
-// y = (P.re - Q.im, P.im + Q.re) at the end.  G groups per thread share each coefficient load.
+// Coefficient pairs A = (Re S[2p][f], Re S[2p+1][f]) and B = (Im S[2p][f], Im S[2p+1][f]) at a
+// 32-bit shared address plus an immediate offset; volatile so that the compiler re-reads them
+// (one broadcast per warp) instead of hoisting a phase's 256 coefficients into registers.
+template <int OFF>
+__device__ __forceinline__ void lds_coef(unsigned addr, unsigned long long &A, unsigned long long &B)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2+%3];\n" : "=l"(A), "=l"(B) : "r"(addr), "n"(OFF));
+}
+
+// Two-qubit phase on every 16-member group, y_e = sum_f S[e][f] x_f, input-stationary: each
+// thread keeps its group's 16 outputs as 8 packed pairs (Re y_2p, Re y_2p+1) and
+// (Im y_2p, Im y_2p+1), streams the 16 inputs once, and for every input and output pair
+// issues four packed FMAs against one 16-byte coefficient load:
+//   Re += A (xr, xr) + B (-xi, -xi),   Im += A (xi, xi) + B (xr, xr).
+// G groups per thread share each coefficient load.
 template <int G, int NT = kTileThreads, bool UNROLL = true>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
@@ -78,54 +88,54 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
             if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
     const unsigned ng = 1u << (TB - 4);
     const unsigned sbase = smem_u32(S);
-    unsigned long long *t64 = reinterpret_cast<unsigned long long *>(tile);
     for (unsigned g0 = threadIdx.x; g0 < ng; g0 += G * NT) {
         unsigned base[G];
-        unsigned long long x[G][16];
 #pragma unroll
-        for (int j = 0; j < G; j++) {
-            unsigned g = g0 + j * NT;
-            base[j] = ins0u(ins0u(ins0u(ins0u(g, p[0]), p[1]), p[2]), p[3]);
+        for (int j = 0; j < G; j++) base[j] = ins0u(ins0u(ins0u(ins0u(g0 + j * NT, p[0]), p[1]), p[2]), p[3]);
+        unsigned long long R[G][8], I[G][8];
 #pragma unroll
-            for (int e = 0; e < 16; e++)
-                x[j][e] = t64[base[j] + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) +
-                              ((e & 1) ? d3 : 0u)];
-        }
-        // Member loop: fully unrolled (UNROLL) the member offsets are compile-time sums of
-        // d0..d3; rolled it needs fewer registers.
-#pragma unroll(UNROLL ? 16 : 1)
-        for (int e = 0; e < 16; e++) {
-            const unsigned oe = ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u);
-            const unsigned se = sbase + 256u * (unsigned)e;  // row e: 16 entries x 16 bytes
-            unsigned long long P0[G], Q0[G], P1[G], Q1[G];
+        for (int j = 0; j < G; j++)
 #pragma unroll
-            for (int j = 0; j < G; j++) P0[j] = Q0[j] = P1[j] = Q1[j] = 0ull;
-#define QCW_PHASE2_STEP(F)                                                   \
+            for (int q = 0; q < 8; q++) R[j][q] = I[j][q] = 0ull;
+#define QCW_PHASE2_PAIR(Q)                                                   \
     {                                                                        \
-        unsigned long long crr, cii;                                         \
-        lds_coef<16 * (F)>(se, crr, cii);                                    \
+        unsigned long long A, B;                                             \
+        lds_coef<16 * (Q)>(sf, A, B);                                        \
         _Pragma("unroll") for (int j = 0; j < G; j++)                        \
         {                                                                    \
-            if ((F) & 1) {                                                   \
-                P1[j] = ffma2(crr, x[j][(F)], P1[j]);                        \
-                Q1[j] = ffma2(cii, x[j][(F)], Q1[j]);                        \
-            } else {                                                         \
-                P0[j] = ffma2(crr, x[j][(F)], P0[j]);                        \
-                Q0[j] = ffma2(cii, x[j][(F)], Q0[j]);                        \
-            }                                                                \
+            R[j][(Q)] = ffma2(A, xrr[j], R[j][(Q)]);                         \
+            R[j][(Q)] = ffma2(B, nxi[j], R[j][(Q)]);                         \
+            I[j][(Q)] = ffma2(A, xii[j], I[j][(Q)]);                         \
+            I[j][(Q)] = ffma2(B, xrr[j], I[j][(Q)]);                         \
         }                                                                    \
     }
-            QCW_PHASE2_STEP(0) QCW_PHASE2_STEP(1) QCW_PHASE2_STEP(2) QCW_PHASE2_STEP(3)
-            QCW_PHASE2_STEP(4) QCW_PHASE2_STEP(5) QCW_PHASE2_STEP(6) QCW_PHASE2_STEP(7)
-            QCW_PHASE2_STEP(8) QCW_PHASE2_STEP(9) QCW_PHASE2_STEP(10) QCW_PHASE2_STEP(11)
-            QCW_PHASE2_STEP(12) QCW_PHASE2_STEP(13) QCW_PHASE2_STEP(14) QCW_PHASE2_STEP(15)
-#undef QCW_PHASE2_STEP
+#pragma unroll(UNROLL ? 16 : 1)
+        for (int f = 0; f < 16; f++) {
+            const unsigned of = ((f & 8) ? d0 : 0u) + ((f & 4) ? d1 : 0u) + ((f & 2) ? d2 : 0u) + ((f & 1) ? d3 : 0u);
+            unsigned long long xrr[G], xii[G], nxi[G];
 #pragma unroll
             for (int j = 0; j < G; j++) {
-                const float2 P = unpack2(fadd2(P0[j], P1[j])), Q = unpack2(fadd2(Q0[j], Q1[j]));
-                tile[base[j] + oe] = make_float2(P.x - Q.y, P.y + Q.x);
+                const float2 v = tile[base[j] + of];
+                xrr[j] = pack2(v.x, v.x);
+                xii[j] = pack2(v.y, v.y);
+                nxi[j] = pack2(-v.y, -v.y);
             }
+            const unsigned sf = sbase + 128u * (unsigned)f;  // input f: 8 pairs x 16 bytes
+            QCW_PHASE2_PAIR(0) QCW_PHASE2_PAIR(1) QCW_PHASE2_PAIR(2) QCW_PHASE2_PAIR(3)
+            QCW_PHASE2_PAIR(4) QCW_PHASE2_PAIR(5) QCW_PHASE2_PAIR(6) QCW_PHASE2_PAIR(7)
         }
+#undef QCW_PHASE2_PAIR
+        // every input of the group has been read: write the outputs in place
+#pragma unroll
+        for (int j = 0; j < G; j++)
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const float2 re = unpack2(R[j][q]), im = unpack2(I[j][q]);
+                const int e0 = 2 * q, e1 = 2 * q + 1;
+                tile[base[j] + ((e0 & 8) ? d0 : 0u) + ((e0 & 4) ? d1 : 0u) + ((e0 & 2) ? d2 : 0u)] = make_float2(re.x, im.x);
+                tile[base[j] + ((e1 & 8) ? d0 : 0u) + ((e1 & 4) ? d1 : 0u) + ((e1 & 2) ? d2 : 0u) + d3] =
+                    make_float2(re.y, im.y);
+            }
     }
 }
 
