@@ -1,0 +1,78 @@
+// Test-only C shim around the fusion planner (host code of the library): plans an op list and
+// returns the phases it produced, so that a CPU test can replay them against the oracle.
+#include <cstring>
+#include <vector>
+
+#include "planner.h"
+
+using namespace qcw;
+
+extern "C" int planner_phases(int n, int kmax, int nops, const int *kind, const int *k, const int *qubits,
+                              const double *mats, const long long *mat_off, int max_phases, int *phase_pass,
+                              int *phase_nq, int *phase_q, int *phase_product, double *phase_S, int *pass_nq)
+{
+    std::vector<QOp> ops(nops);
+    for (int i = 0; i < nops; i++) {
+        QOp &o = ops[i];
+        o.kind = kind[i];
+        o.k = k[i];
+        o.ncontrols = 0;
+        for (int j = 0; j < o.k; j++) o.qubits[j] = qubits[2 * i + j];
+        const int dim = o.kind == 0 ? (1 << o.k) : (1 << (2 * o.k));
+        o.m.resize((size_t)dim * dim);
+        for (int t = 0; t < dim * dim; t++)
+            o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
+    }
+    std::vector<PassPlan> plan = plan_passes(ops, 0, ops.size(), n, kmax);
+    int np = 0;
+    for (size_t p = 0; p < plan.size(); p++) {
+        pass_nq[p] = (int)plan[p].Q.size();
+        for (const PhasePlan &ph : plan[p].phases) {
+            if (np >= max_phases) return -1;
+            phase_pass[np] = (int)p;
+            phase_nq[np] = ph.nq;
+            phase_product[np] = ph.product ? 1 : 0;
+            phase_q[2 * np] = ph.qa;
+            phase_q[2 * np + 1] = ph.qb;
+            for (size_t t = 0; t < ph.S.size() && t < 256; t++) {
+                phase_S[512 * (size_t)np + 2 * t] = ph.S[t].real();
+                phase_S[512 * (size_t)np + 2 * t + 1] = ph.S[t].imag();
+            }
+            np++;
+        }
+    }
+    return np * 1000 + (int)plan.size();
+}
+
+// Pass / phase structure of the count-only plan (used by the fusion-width search) against the
+// full plan of the same ops: returns the number of mismatching fields (0 when they agree).
+extern "C" int planner_count_only_mismatch(int n, int kmax, int nops, const int *kind, const int *k,
+                                           const int *qubits, const double *mats, const long long *mat_off)
+{
+    std::vector<QOp> ops(nops);
+    for (int i = 0; i < nops; i++) {
+        QOp &o = ops[i];
+        o.kind = kind[i];
+        o.k = k[i];
+        o.ncontrols = 0;
+        for (int j = 0; j < o.k; j++) o.qubits[j] = qubits[2 * i + j];
+        const int dim = o.kind == 0 ? (1 << o.k) : (1 << (2 * o.k));
+        o.m.resize((size_t)dim * dim);
+        for (int t = 0; t < dim * dim; t++)
+            o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
+    }
+    const std::vector<PassPlan> a = plan_passes(ops, 0, ops.size(), n, kmax);
+    const std::vector<PassPlan> b = plan_passes(ops, 0, ops.size(), n, kmax, true);
+    int bad = a.size() != b.size();
+    for (size_t p = 0; p < a.size() && p < b.size(); p++) {
+        bad += a[p].Q != b[p].Q;
+        bad += a[p].nops != b[p].nops;
+        bad += a[p].phases.size() != b[p].phases.size();
+        for (size_t i = 0; i < a[p].phases.size() && i < b[p].phases.size(); i++) {
+            const PhasePlan &x = a[p].phases[i], &y = b[p].phases[i];
+            bad += x.nq != y.nq || x.product != y.product || x.qa != y.qa || x.qb != y.qb || x.nops != y.nops;
+            bad += !y.S.empty();
+        }
+    }
+    return bad;
+}

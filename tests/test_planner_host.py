@@ -1,0 +1,171 @@
+"""CPU test of the fusion planner (host code): its passes and composed phase superoperators,
+replayed in order with numpy, must reproduce the oracle applying the original operations in
+order (up to complex128 rounding).  This checks the commutation-based reordering, the phase
+composition and the product-phase split without a GPU."""
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from tests._helpers import haar_unitary, random_rho
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1101_1785_gb300", "csrc")
+SHIM = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cpp", "planner_shim.cpp")
+
+
+def _cuda_include():
+    for d in ("/usr/local/cuda/include",):
+        if os.path.exists(os.path.join(d, "cuda_runtime.h")):
+            return d
+    pytest.skip("CUDA headers not found")
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("planner") / "libplanner_shim.so")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-I", os.path.join(ROOT, "include"),
+                           "-I", CSRC, "-I", _cuda_include(), "-o", out, SHIM, os.path.join(CSRC, "planner.cpp")])
+    lib = ctypes.CDLL(out)
+    lib.planner_phases.restype = ctypes.c_int
+    lib.planner_count_only_mismatch.restype = ctypes.c_int
+    return lib
+
+
+def _superop_kraus(ks):
+    return sum(np.kron(K, K.conj()) for K in ks)
+
+
+def _random_ops(rng, n, count):
+    ops = []
+    for _ in range(count):
+        r = rng.random()
+        if r < 0.4:
+            ops.append(("u", (int(rng.integers(n)),), haar_unitary(rng, 2)))
+        elif r < 0.6:
+            a, b = [int(x) for x in rng.permutation(n)[:2]]
+            ops.append(("u", (a, b), haar_unitary(rng, 4)))
+        elif r < 0.9:
+            q = int(rng.integers(n))
+            ks = [np.sqrt(w) * haar_unitary(rng, 2) for w in (0.7, 0.3)]
+            ops.append(("k", (q,), ks))
+        else:
+            a, b = [int(x) for x in rng.permutation(n)[:2]]
+            ks = [np.sqrt(w) * haar_unitary(rng, 4) for w in (0.5, 0.5)]
+            ops.append(("k", (a, b), ks))
+    return ops
+
+
+def _marshal(ops):
+    """Op arrays in the shim's layout: kind, k, qubits (two per op), matrices, offsets."""
+    kinds = np.array([0 if o[0] == "u" else 1 for o in ops], dtype=np.int32)
+    ks = np.array([len(o[1]) for o in ops], dtype=np.int32)
+    qs = np.zeros(2 * len(ops), dtype=np.int32)
+    mats, offs, off = [], [], 0
+    for i, o in enumerate(ops):
+        qs[2 * i:2 * i + len(o[1])] = o[1]
+        m = o[2] if o[0] == "u" else _superop_kraus(o[2])
+        mats.append(np.ascontiguousarray(m, dtype=np.complex128).ravel())
+        offs.append(off)
+        off += m.size
+    return kinds, ks, qs, np.concatenate(mats), np.array(offs, dtype=np.int64)
+
+
+def _plan(shim, n, kmax, ops):
+    kinds, ks, qs, mats, offs = _marshal(ops)
+    maxp = 4 * len(ops) + 8
+    pp = np.zeros(maxp, np.int32)
+    pnq = np.zeros(maxp, np.int32)
+    pq = np.zeros(2 * maxp, np.int32)
+    pprod = np.zeros(maxp, np.int32)
+    pS = np.zeros(512 * maxp, np.float64)
+    passq = np.zeros(maxp, np.int32)
+    P = ctypes.c_void_p
+    r = shim.planner_phases(n, kmax, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P), qs.ctypes.data_as(P),
+                            mats.ctypes.data_as(P), offs.ctypes.data_as(P), maxp, pp.ctypes.data_as(P),
+                            pnq.ctypes.data_as(P), pq.ctypes.data_as(P), pprod.ctypes.data_as(P),
+                            pS.ctypes.data_as(P), passq.ctypes.data_as(P))
+    assert r >= 0
+    nph, npass = r // 1000, r % 1000
+    phases = []
+    for i in range(nph):
+        S = pS[512 * i:512 * i + 512].view(np.complex128)
+        phases.append((int(pp[i]), int(pnq[i]), (int(pq[2 * i]), int(pq[2 * i + 1])), bool(pprod[i]), S.copy()))
+    return phases, passq[:npass]
+
+
+def _apply_superop(rho, n, S, qubits):
+    """rho <- S acting on (row bits, column bits) of `qubits`; index (R, C) with R, C the
+    binary numbers of the qubits' row / column bits (first qubit most significant)."""
+    k = len(qubits)
+    t = rho.reshape([2] * (2 * n))
+    S = S.reshape([2] * (4 * k))
+    letters = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"
+    src = list(letters[:2 * n])
+    out = list(src)
+    new = letters[2 * n:2 * n + 2 * k]
+    s_out = []
+    s_in = []
+    for j, q in enumerate(qubits):  # row bits
+        s_in.append(src[q])
+        s_out.append(new[j])
+        out[q] = new[j]
+    for j, q in enumerate(qubits):  # column bits
+        s_in.append(src[n + q])
+        s_out.append(new[k + j])
+        out[n + q] = new[k + j]
+    expr = "".join(s_out) + "".join(s_in) + "," + "".join(src) + "->" + "".join(out)
+    return np.einsum(expr, S, t).reshape(rho.shape)
+
+
+@pytest.mark.parametrize("n,kmax,seed", [(3, 2, 1), (4, 3, 2), (5, 4, 3), (6, 5, 4), (6, 2, 5)])
+def test_planner_replay_matches_oracle(shim, n, kmax, seed):
+    rng = np.random.default_rng(seed)
+    ops = _random_ops(rng, n, 60)
+    rho0 = random_rho(rng, n)
+    want = rho0.copy()
+    for kind, qs, m in ops:
+        if kind == "u":
+            oracle.apply_unitary(want, m, qs)
+        else:
+            oracle.apply_kraus(want, np.stack(m), qs)
+    phases, pass_nq = _plan(shim, n, kmax, ops)
+    assert (pass_nq <= kmax).all() and len(pass_nq) >= 1
+    got = rho0.copy()
+    for _, nq, (qa, qb), product, S in phases:
+        if nq == 1:
+            got = _apply_superop(got, n, S[:16], (qa,))
+        elif product:
+            got = _apply_superop(got, n, S[:16], (qa,))
+            got = _apply_superop(got, n, S[16:32], (qb,))
+        else:
+            got = _apply_superop(got, n, S, (qa, qb))
+    assert np.abs(got - want).max() < 1e-12
+
+
+def test_planner_packs_disjoint_work(shim):
+    """Ops on disjoint qubits commute: a run alternating between two qubit pairs fits one pass."""
+    rng = np.random.default_rng(9)
+    ops = []
+    for i in range(20):
+        pair = (0, 1) if i % 2 == 0 else (2, 3)
+        ops.append(("u", pair, haar_unitary(rng, 4)))
+    phases, pass_nq = _plan(shim, 4, 4, ops)
+    assert len(pass_nq) == 1 and len(phases) == 2
+
+
+@pytest.mark.parametrize("n,kmax", [(5, 3), (8, 4), (10, 5)])
+def test_count_only_plan_has_the_same_structure(shim, n, kmax):
+    """The width search plans without composing superoperators; its passes and phases must be
+    the ones the full plan produces."""
+    rng = np.random.default_rng(n * 31 + kmax)
+    ops = _random_ops(rng, n, 120)
+    kinds, ks, qs, mats, offs = _marshal(ops)
+    P = ctypes.c_void_p
+    bad = shim.planner_count_only_mismatch(n, kmax, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P),
+                                           qs.ctypes.data_as(P), mats.ctypes.data_as(P), offs.ctypes.data_as(P))
+    assert bad == 0
