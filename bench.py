@@ -51,7 +51,7 @@ def parse_args():
                          "one launch; serve: Poisson request stream through the continuous-batching server")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
-    ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "herm"],
+    ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "herm", "herm_ws"],
                     help="kernel for large fused passes (results are identical)")
     ap.add_argument("--fuse-k", type=int, default=FUSE_K, help="qubits per fused pass")
     ap.add_argument("--qubits", type=int, default=N_QUBITS,
@@ -157,6 +157,10 @@ def herm_pass_bytes(n, tile_qubits=6):
     return tile * (m * (m + 1) // 2 + m * m)
 
 
+TIMED_KERNEL = {"auto": "k_fused_herm_ws", "herm_ws": "k_fused_herm_ws", "herm": "k_fused_herm",
+                "tile": "k_fused_pass"}
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in ("fused.cu", "planner.cpp", "qcw_device.cuh", "tile.cuh", "tile.cpp"):
@@ -256,7 +260,7 @@ def run_ours(args):
     packed = [q.PackedOps(p) for p in parts]
     d = q.Density(nq)
     d.set_mode(q.QCW_MODE_FUSED, args.fuse_k)
-    d.set_fused_kernel({"auto": 0, "tile": 1, "herm": 2}[args.fused_kernel])
+    d.set_fused_kernel({"auto": 0, "tile": 1, "herm": 2, "herm_ws": 3}[args.fused_kernel])
     rho_ptr, stream_ptr = d.device_state()
     ext = torch.cuda.ExternalStream(stream_ptr)
 
@@ -339,7 +343,7 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({8 * 4 ** nq / 2**20:.0f} MiB rho vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": recorded_traffic(),
-                         "peak_kind": peak_kind, "kernel": "k_fused_herm",
+                         "peak_kind": peak_kind, "kernel": TIMED_KERNEL[args.fused_kernel],
                          "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (4 ** nq),

@@ -83,16 +83,30 @@ QCW_API qcw_status qcw_destroy(qcw_ctx *ctx);
 QCW_API qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k);
 
 /* Which kernel runs fused passes.
- *   HERM (and AUTO, the default): rho is a density matrix, hence Hermitian (Sec. 5.2, rho^dagger
- *     = rho).  Tiles hold the row and column bits of the same qubits; each pass evolves the
- *     tiles on one side of the diagonal and writes the others as their conjugate transposes
- *     (half the arithmetic).  A non-Hermitian matrix loaded with qcw_set_state is not preserved.
+ *   HERM: rho is a density matrix, hence Hermitian (Sec. 5.2, rho^dagger = rho).  Tiles hold
+ *     the row and column bits of the same qubits; each pass evolves the tiles on one side of
+ *     the diagonal and writes the others as their conjugate transposes (half the arithmetic).
+ *     A non-Hermitian matrix loaded with qcw_set_state is not preserved.  One CTA per tile.
+ *   HERM_WS (and AUTO, the default): the same Hermitian pass on persistent CTAs whose
+ *     producer warp loads and stores tiles while consumer warps evolve them, so memory traffic
+ *     and arithmetic overlap.  Used for registers of 6 or more qubits (HERM below that).
  *   TILE: one CTA per tile, no symmetry assumed.
  * Flushes queued work first. */
 #define QCW_FUSED_KERNEL_AUTO 0
 #define QCW_FUSED_KERNEL_TILE 1
 #define QCW_FUSED_KERNEL_HERM 2
+#define QCW_FUSED_KERNEL_HERM_WS 3
 QCW_API qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which);
+
+/* Bounded waits inside the HERM_WS pass kernel.  Producer and consumer warps hand tiles over
+ * through shared-memory barriers; each wait gives up after `polls` polls (0 restores the
+ * default, about half a second or more), sets the context's error word and ends the kernel.
+ * The next qcw_sync or readout then returns QCW_ETIMEOUT, and keeps doing so until qcw_reset or
+ * a state load (rho is undefined after such a pass).  stall_tile >= 0 makes the first CTA skip
+ * the load of its tile number stall_tile, so that its consumers' wait runs out (a test of the
+ * error path without any fault); -1 turns that off.  The paper has no counterpart.
+ * Flushes queued work first.  QCW_EINVAL if stall_tile < -1. */
+QCW_API qcw_status qcw_set_fused_wait_limit(qcw_ctx *ctx, unsigned polls, int stall_tile);
 
 /* Device pointer of rho and the context's stream (borrowed; valid until destroy). */
 QCW_API qcw_status qcw_get_device_state(qcw_ctx *ctx, void **dev_rho, void **cuda_stream);

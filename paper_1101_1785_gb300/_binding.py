@@ -40,6 +40,7 @@ SIGNATURES = {
     "qcw_destroy": (I, [P]),
     "qcw_set_mode": (I, [P, I, I]),
     "qcw_set_fused_kernel": (I, [P, I]),
+    "qcw_set_fused_wait_limit": (I, [P, ctypes.c_uint, I]),
     "qcw_get_device_state": (I, [P, PP, PP]),
     "qcw_nqubits": (I, [P]),
     "qcw_reset": (I, [P]),
@@ -206,8 +207,14 @@ class Density:
         check(lib().qcw_set_mode(self.h, int(mode), int(fuse_k)), "qcw_set_mode")
 
     def set_fused_kernel(self, which: int):
-        """0 = auto (Hermitian), 1 = one CTA per tile (no symmetry assumed), 2 = Hermitian."""
+        """0 = auto (warp-specialised Hermitian from 6 qubits), 1 = one CTA per tile (no symmetry
+        assumed), 2 = Hermitian, one CTA per tile pair, 3 = warp-specialised Hermitian."""
         check(lib().qcw_set_fused_kernel(self.h, int(which)), "qcw_set_fused_kernel")
+
+    def set_fused_wait_limit(self, polls: int, stall_tile: int = -1):
+        """Poll limit of the fused kernel's in-kernel waits (0 = default) and an optional tile
+        whose load the first CTA skips, so that the wait runs out."""
+        check(lib().qcw_set_fused_wait_limit(self.h, int(polls), int(stall_tile)), "qcw_set_fused_wait_limit")
 
     def device_state(self):
         r, s = P(), P()

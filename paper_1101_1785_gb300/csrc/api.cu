@@ -245,6 +245,7 @@ static qcw_status ctx_common(qcw_ctx *c)
         return set_error(QCW_ENOMEM, "reduction scratch");
     if (cudaMalloc(&c->d_result, 64 * sizeof(double)) != cudaSuccess) return set_error(QCW_ENOMEM, "result block");
     if (cudaMallocHost(&c->h_result, 64 * sizeof(double)) != cudaSuccess) return set_error(QCW_ENOMEM, "pinned result");
+    CK(cudaMemset(c->d_result, 0, 64 * sizeof(double)));
     return QCW_OK;
 }
 
@@ -309,7 +310,7 @@ extern "C" int qcw_nqubits(const qcw_ctx *ctx) { return ctx ? ctx->n : -1; }
 extern "C" qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which)
 {
     CHECK_CTX(ctx);
-    if (which < QCW_FUSED_KERNEL_AUTO || which > QCW_FUSED_KERNEL_HERM) return set_error(QCW_EINVAL, "bad kernel choice");
+    if (which < QCW_FUSED_KERNEL_AUTO || which > QCW_FUSED_KERNEL_HERM_WS) return set_error(QCW_EINVAL, "bad kernel choice");
     qcw_status st = fused_flush(ctx);
     if (st) return st;
     ctx->fused_kernel = which;
@@ -337,10 +338,37 @@ extern "C" qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k)
 }
 
 // ------------------------------------------------------------------ state
+// A fused pass whose in-kernel wait ran out left rho undefined: the error word stays set (and
+// readouts fail) until the state is replaced.
+static qcw_status clear_error_word(qcw_ctx *c)
+{
+    CK(cudaMemsetAsync(device_error_word(c), 0, sizeof(unsigned long long), c->stream));
+    return QCW_OK;
+}
+
+static qcw_status check_error_word(qcw_ctx *c, unsigned long long word)
+{
+    if (word) return set_error(QCW_ETIMEOUT, "fused pass: an in-kernel wait ran out; rho is undefined until reset");
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_set_fused_wait_limit(qcw_ctx *ctx, unsigned polls, int stall_tile)
+{
+    CHECK_CTX(ctx);
+    if (stall_tile < -1) return set_error(QCW_EINVAL, "bad stall tile");
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    ctx->wait_limit = polls;
+    ctx->stall_tile = stall_tile;
+    return QCW_OK;
+}
+
 extern "C" qcw_status qcw_reset(qcw_ctx *ctx)
 {
     CHECK_CTX(ctx);
     ctx->queue.clear();
+    qcw_status st = clear_error_word(ctx);
+    if (st) return st;
     launch_zero_state(ctx->rho, ctx->n, ctx->nsm, ctx->stream);
     CKLAUNCH(ctx, 1);
     return QCW_OK;
@@ -367,6 +395,8 @@ extern "C" qcw_status qcw_set_state(qcw_ctx *ctx, const double *rho_c128)
     qcw_status st = ensure_staging(ctx);
     if (st) return st;
     ctx->queue.clear();
+    st = clear_error_word(ctx);
+    if (st) return st;
     size_t total = (size_t)1 << (2 * ctx->n);
     for (size_t off = 0; off < total; off += kStageElems) {
         size_t cnt = total - off < kStageElems ? total - off : kStageElems;
@@ -384,6 +414,8 @@ extern "C" qcw_status qcw_set_state_c64(qcw_ctx *ctx, const float *rho_c64)
     CHECK_CTX(ctx);
     if (!rho_c64) return set_error(QCW_EINVAL, "null state");
     ctx->queue.clear();
+    qcw_status st = clear_error_word(ctx);
+    if (st) return st;
     size_t bytes = sizeof(float2) << (2 * ctx->n);
     CK(cudaMemcpyAsync(ctx->rho, rho_c64, bytes, cudaMemcpyHostToDevice, ctx->stream));
     return QCW_OK;
@@ -549,20 +581,31 @@ extern "C" qcw_status qcw_sync(qcw_ctx *ctx)
     CHECK_CTX(ctx);
     qcw_status st = fused_flush(ctx);
     if (st) return st;
+    CK(cudaMemcpyAsync(ctx->h_result + kErrSlot, device_error_word(ctx), sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    return QCW_OK;
+    unsigned long long w;
+    memcpy(&w, ctx->h_result + kErrSlot, sizeof w);
+    return check_error_word(ctx, w);
 }
 
 // ------------------------------------------------------------------ readouts
+// Copy the result block (with the error word) to the pinned mirror and wait for it.
+static qcw_status fetch_results(qcw_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->h_result, c->d_result, 64 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    unsigned long long w;
+    memcpy(&w, c->h_result + kErrSlot, sizeof w);
+    return check_error_word(c, w);
+}
 static qcw_status diag_readout(qcw_ctx *c)
 {
     qcw_status st = fused_flush(c);
     if (st) return st;
     launch_diag_reduce(c->rho, c->n, c->d_partials, c->d_result, c->red_blocks, c->stream);
     CKLAUNCH(c, launches_per_reduce());
-    CK(cudaMemcpyAsync(c->h_result, c->d_result, sizeof(double) * (c->n + 2), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return QCW_OK;
+    return fetch_results(c);
 }
 
 extern "C" qcw_status qcw_trace(qcw_ctx *ctx, double *re, double *im)
@@ -593,8 +636,8 @@ extern "C" qcw_status qcw_purity(qcw_ctx *ctx, double *out)
     if (st) return st;
     launch_purity(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
     CKLAUNCH(ctx, launches_per_reduce());
-    CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    st = fetch_results(ctx);
+    if (st) return st;
     *out = ctx->h_result[0];
     return QCW_OK;
 }

@@ -65,6 +65,7 @@ struct KTune {
 struct FusedRuntime {
     std::vector<CachedPlan> cache;
     long long tick = 0;
+    unsigned ws_grid = 0;  // CTAs of the warp-specialised kernel (resident per SM x SMs)
     std::vector<cudaEvent_t> ev_free, ev_pending;  // pairs: start, stop
     KTune tune;
 };
@@ -158,7 +159,7 @@ __device__ __forceinline__ void herm_mirror(float2 *__restrict__ rho, const FPas
         const unsigned Rp = u & hmask, Chi = u >> h;
         const unsigned tp = (Rp << h) | (Chi << J) | j;
         const unsigned ts = (((Chi << J) | j) << h) | Rp;
-        const float2 v = tile[ts];
+        const float2 v = tile[herm_phys(ts)];
         rho[mbase + hoff[tp >> L] + (tp & lmask)] = make_float2(v.x, -v.y);
     }
 }
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const FPass &P = passes[pass_idx];
-    const int TB = P.TB, L = P.L, h = P.TB / 2, m = P.nother / 2;
+    const int TB = P.TB, L = P.L, m = P.nother / 2;
     const TileSmem sm = tile_smem(smem, TB, L);
     tile_hoff_nt<HT>(P, sm.hoff);
     // The evolved tile is the one with o_c <= o_r (on or below the diagonal): consecutive CTAs
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
         const unsigned nvec = 1u << (TB - 1), lmask = (1u << L) - 1u;
         for (unsigned v = threadIdx.x; v < nvec; v += HT) {
             unsigned e = 2 * v;
-            cp_async16(&sm.tile[e], rho + base + sm.hoff[e >> L] + (e & lmask));
+            cp_async16(&sm.tile[herm_phys(e)], rho + base + sm.hoff[e >> L] + (e & lmask));
         }
         cp_async_wait_all();
         __syncthreads();
@@ -194,17 +195,163 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
         const int ncoef = phase_coefs(F.nq);
         for (int i = threadIdx.x; i < ncoef; i += HT) sm.S[i] = coefs[F.coef + i];
         __syncthreads();
-        tile_apply_phase<HT, false>(sm.tile, TB, F, sm.S);
+        tile_apply_phase<HT, false, true>(sm.tile, TB, F, sm.S);
         __syncthreads();
     }
-    tile_store_nt<HT>(rho, P, t_self, sm.tile, sm.hoff);
+    tile_store_nt<HT, true>(rho, P, t_self, sm.tile, sm.hoff);
     if (o_r == o_c) return;
     herm_mirror<HT>(rho, P, tile_base(P, ((uint64_t)o_c << m) | o_r), sm.tile, sm.hoff);
 }
 
+// ------------------------------------------------------------------ warp-specialised Hermitian pass
+// Persistent CTAs (three per SM) of four consumer warps and one producer warp sharing two tile
+// buffers.  CTA c takes the pairs c, c + grid, c + 2 grid, ...  The producer loads the next
+// pair's lower-triangle tile with cp.async while the consumers evolve the current one, and
+// writes evolved tiles (and their conjugate-transposed mirrors) back while the consumers work
+// on the next, so the pass's HBM traffic overlaps its arithmetic instead of adding to it.
+// Hand-over is by mbarriers: full[b] (the 32 producer lanes' cp.async arrivals) and empty[b]
+// (the 128 consumers' arrivals).  Every wait is bounded: on running out, the side that gave up
+// sets the pass's error word and returns, and the other side then runs out too.
+//
+// Tiles are 2^12 elements (six qubits); the producer's lane covers tile bits 0..5 (an element
+// pair) and its loop index k the bits 6..11, so global offsets and swizzled shared-memory
+// positions split into a per-lane part and a per-k part read from a 64-entry table.
+constexpr int WC = 128;                 // consumer threads
+constexpr int WTH = WC + 32;            // plus the producer warp
+constexpr int kWsCtasPerSm = 3;
+constexpr unsigned kWsWaitLimit = 1u << 21;  // polls (>= 0.5 s with the 256 ns back-off)
+
+struct WsEntry {
+    unsigned long long ghi;  // global offset of tile bits 6..11 = k
+    unsigned phi;            // herm_phys(k << 6)
+    unsigned pm;             // herm_phys(k)
+};
+
+static size_t ws_smem_bytes()
+{
+    return 2 * (sizeof(float2) << 12) + 64 * sizeof(WsEntry) + 256 * sizeof(float2) + 4 * sizeof(uint64_t);
+}
+
+__global__ void __launch_bounds__(WTH, kWsCtasPerSm)
+    k_fused_herm_ws(float2 *__restrict__ rho, const FPass *__restrict__ passes, const FPhase *__restrict__ phases,
+                    const float2 *__restrict__ coefs, int pass_idx, unsigned npairs,
+                    unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *buf = reinterpret_cast<float2 *>(smem);  // two tiles of 2^12 elements
+    WsEntry *tab = reinterpret_cast<WsEntry *>(buf + 2 * 4096);
+    float2 *S = reinterpret_cast<float2 *>(tab + 64);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(S + 256);  // full0, full1, empty0, empty1
+    const FPass &P = passes[pass_idx];
+    const int m = P.nother / 2;
+    const unsigned tid = threadIdx.x;
+    if (tid < 64) {
+        unsigned long long g = 0;
+        for (int j = 0; j < 6; j++)
+            if ((tid >> j) & 1u) g += 1ull << P.tbits[6 + j];
+        tab[tid].ghi = g;
+        tab[tid].phi = herm_phys(tid << 6);
+        tab[tid].pm = herm_phys(tid);
+    }
+    if (tid == 0) {
+        mbar_init(&bars[0], 32);
+        mbar_init(&bars[1], 32);
+        mbar_init(&bars[2], WC);
+        mbar_init(&bars[3], WC);
+    }
+    __syncthreads();
+    const unsigned ntile = blockIdx.x < npairs ? (npairs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (tid >= WC) {  // ---- producer warp
+        const unsigned lane = tid - WC;
+        unsigned long long glo = 0;  // global offset of element 2 lane of a tile (bits 0..5)
+        for (int j = 0; j < 6; j++)
+            if (((2 * lane) >> j) & 1u) glo += 1ull << P.tbits[j];
+        const unsigned plo = herm_phys(2 * lane);
+        const unsigned pm0 = herm_phys((2 * lane) << 6), pm1 = herm_phys((2 * lane + 1) << 6);
+        auto pair_bases = [&](unsigned i, uint64_t &self, uint64_t &mirror) {
+            unsigned o_r, o_c;
+            pair_of(blockIdx.x + i * gridDim.x, o_c, o_r);
+            self = tile_base(P, ((uint64_t)o_r << m) | o_c) + glo;
+            mirror = o_r != o_c ? tile_base(P, ((uint64_t)o_c << m) | o_r) + glo : ~0ull;
+        };
+        auto load = [&](unsigned i) {
+            float2 *bf = buf + ((i & 1u) << 12);
+            uint64_t sb, mb;
+            pair_bases(i, sb, mb);
+#pragma unroll 8
+            for (int k = 0; k < 64; k++) {
+                const WsEntry t = tab[k];
+                cp_async16(bf + (plo ^ t.phi), rho + sb + t.ghi);
+            }
+            cp_async_mbar_arrive(&bars[i & 1u]);
+        };
+        // the element pair (t, t + 1) of the mirror is conj of tile elements swap(t), swap(t + 1)
+        auto store = [&](unsigned i) {
+            const float2 *bf = buf + ((i & 1u) << 12);
+            uint64_t sb, mb;
+            pair_bases(i, sb, mb);
+#pragma unroll 4
+            for (int k = 0; k < 64; k++) {
+                const WsEntry t = tab[k];
+                *reinterpret_cast<float4 *>(rho + sb + t.ghi) = *reinterpret_cast<const float4 *>(bf + (plo ^ t.phi));
+                if (mb != ~0ull) {
+                    const float2 a = bf[pm0 ^ t.pm], b = bf[pm1 ^ t.pm];
+                    *reinterpret_cast<float4 *>(rho + mb + t.ghi) = make_float4(a.x, -a.y, b.x, -b.y);
+                }
+            }
+        };
+        bool ok = true;
+        for (unsigned i = 0; i < ntile; i++) {
+            if (i >= 2) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&bars[2 + (i & 1u)], ((i >> 1) - 1) & 1u, wait_limit));
+                if (!ok) break;
+                store(i - 2);
+                __syncwarp();  // the warp's reads of the buffer precede the new copies into it
+            }
+            if (!(blockIdx.x == 0 && (int)i == stall_tile)) load(i);
+        }
+        for (unsigned i = ntile >= 2 ? ntile - 2 : 0; ok && i < ntile; i++) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&bars[2 + (i & 1u)], (i >> 1) & 1u, wait_limit));
+            if (ok) store(i);
+        }
+        cp_async_wait_all();
+        if (!ok && lane == 0) atomicOr(err, 1ull);
+        return;
+    }
+
+    // ---- consumer warps: the pass's phases on each tile in turn
+    bool ok = true;
+    for (unsigned i = 0; i < ntile; i++) {
+        const unsigned b = i & 1u;
+        ok = bar_and(1, WC, mbar_wait(&bars[b], (i >> 1) & 1u, wait_limit));
+        if (!ok) break;
+        float2 *tile = buf + (b << 12);
+        for (int ph = 0; ph < P.nphase; ph++) {
+            const FPhase F = phases[P.phase0 + ph];
+            const int ncoef = phase_coefs(F.nq);
+            for (int j = tid; j < ncoef; j += WC) S[j] = coefs[F.coef + j];
+            bar_sync(1, WC);
+            tile_apply_phase<WC, false, true>(tile, 12, F, S);
+            bar_sync(1, WC);
+        }
+        mbar_arrive(&bars[2 + b]);
+    }
+    if (!ok && tid == 0) atomicOr(err, 2ull);
+}
+
 static bool herm_kernel(const qcw_ctx *c)
 {
-    return c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM;
+    return c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
+           c->fused_kernel == QCW_FUSED_KERNEL_HERM_WS;
+}
+
+// Passes the warp-specialised kernel takes: Hermitian, 2^12-element tiles with column bit 0 of
+// rho inside (element pairs contiguous in global memory).
+static bool ws_pass(const qcw_ctx *c, const FPass &fp)
+{
+    return (c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM_WS) && fp.herm &&
+           fp.TB == 12 && fp.L >= 1;
 }
 
 static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, size_t e, int k, int tbmax,
@@ -341,7 +488,15 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     for (size_t p = 0; p < hit->smem.size(); p++) maxsm = std::max(maxsm, hit->smem[p]);
     qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm), maxsm);
+    if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm_ws), ws_smem_bytes());
     if (sst) return sst;
+    if (!rt->ws_grid) {
+        int per_sm = 0;
+        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, reinterpret_cast<const void *>(k_fused_herm_ws), WTH, ws_smem_bytes());
+        if (oe != cudaSuccess) return cuda_error(oe, "occupancy");
+        rt->ws_grid = (unsigned)std::max(1, per_sm) * (unsigned)c->nsm;
+    }
     if (trial) {
         if (!tn.e0) {
             cudaEventCreate(&tn.e0);
@@ -364,7 +519,12 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             }
             cudaEventRecord(e0, c->stream);
         }
-        if (hit->hpass[p].herm) {
+        if (ws_pass(c, hit->hpass[p])) {
+            const unsigned npairs = (unsigned)hit->grid[p];
+            k_fused_herm_ws<<<std::min(npairs, rt->ws_grid), WTH, ws_smem_bytes(), c->stream>>>(
+                c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), c->wait_limit ? c->wait_limit : kWsWaitLimit,
+                c->stall_tile);
+        } else if (hit->hpass[p].herm) {
             k_fused_herm<<<hit->grid[p], HT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
         } else {
             k_fused_pass<<<hit->grid[p], FT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);

@@ -114,6 +114,10 @@ struct qcw_ctx {
     // fused mode
     std::vector<qcw::QOp> queue;
     qcw::FusedRuntime *fused = nullptr;
+    // bounded in-kernel waits of the fused passes: polls before giving up (0: default) and a
+    // tile whose load the first CTA skips (fault injection; -1: none)
+    unsigned wait_limit = 0;
+    int stall_tile = -1;
     // counters
     long long launches = 0;
     long long passes = 0;
@@ -123,6 +127,13 @@ struct qcw_ctx {
 };
 
 namespace qcw {
+// Device word in the context's result block where kernels report a wait that ran out (bit 0:
+// producer side, bit 1: consumer side).  Sticky until qcw_reset or a state load.
+constexpr int kErrSlot = 63;
+inline unsigned long long *device_error_word(qcw_ctx *c)
+{
+    return reinterpret_cast<unsigned long long *>(c->d_result + kErrSlot);
+}
 // fused.cu / planner.cpp entry points used by the API layer
 qcw_status fused_flush(qcw_ctx *ctx);
 void fused_destroy(qcw_ctx *ctx);

@@ -1,6 +1,8 @@
 // Host side of the tile descriptors: tile bit selection and packing of planner output.
 #include "tile.h"
 
+#include <algorithm>
+
 namespace qcw {
 
 size_t tile_smem_bytes(int TB, int L)
@@ -44,6 +46,32 @@ static int tile_pos(const FPass &fp, int vbit)
     return -1;
 }
 
+// Hermitian passes: enumeration order of the tile bits outside a phase (positions pos[0..np)).
+// The first bits are the ones whose shared-memory bank pairs (bits 0..3 of herm_phys) are
+// linearly independent, so that the 32 groups a warp handles at once spread over all 16
+// bank pairs (8 when bit 0 is a phase bit); the rest follow in ascending order.
+static void herm_group_order(const FPass &fp, FPhase &f, int np)
+{
+    unsigned in_phase = 0;
+    for (int a = 0; a < np; a++) in_phase |= 1u << f.pos[a];
+    int order[16], no = 0;
+    unsigned basis[4];
+    int nb = 0;
+    bool taken[16] = {};
+    for (int b = 0; b < fp.TB && nb < 4; b++) {
+        if (in_phase & (1u << b)) continue;
+        unsigned v = herm_phys(1u << b) & 15u;
+        for (int i = 0; i < nb; i++) v = std::min(v, v ^ basis[i]);
+        if (!v) continue;
+        basis[nb++] = v;
+        order[no++] = b;
+        taken[b] = true;
+    }
+    for (int b = 0; b < fp.TB; b++)
+        if (!(in_phase & (1u << b)) && !taken[b]) order[no++] = b;
+    for (int i = 0; i < no && i < 12; i++) f.opos[i] = (int8_t)order[i];
+}
+
 void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TilePlan &out, bool herm)
 {
     for (const PassPlan &pp : plan) {
@@ -67,6 +95,7 @@ void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TileP
                 f.pos[1] = (int8_t)tile_pos(fp, n - 1 - ph.qa);
                 out.nphase1++;
             }
+            if (herm) herm_group_order(fp, f, ph.nq == 2 ? 4 : 2);
             if (ph.S.empty()) {
                 // structure-only plan (width search): no coefficients
             } else if (f.nq == PH_TWO) {

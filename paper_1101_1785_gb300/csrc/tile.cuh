@@ -69,17 +69,46 @@ __device__ __forceinline__ void lds_coef(unsigned addr, unsigned long long &A, u
     asm volatile("ld.shared.v2.b64 {%0, %1}, [%2+%3];\n" : "=l"(A), "=l"(B) : "r"(addr), "n"(OFF));
 }
 
+// Shared-memory offset of the first member of group g of a phase (members then differ by the
+// phase deltas).  SWZ (Hermitian passes, swizzled tile): g's bits go to the phase's outside
+// bits in the order opos lists them and the result is mapped by herm_phys; otherwise they go
+// to the outside bits in ascending order (insert a zero at each sorted phase position).
+template <bool SWZ, int NPOS>
+__device__ __forceinline__ unsigned group_base(unsigned g, const FPhase &F, const int (&p)[NPOS], int nout)
+{
+    if (SWZ) {
+        unsigned b = 0;
+#pragma unroll
+        for (int i = 0; i < 12; i++)
+            if (i < nout) b |= ((g >> i) & 1u) << F.opos[i];
+        return herm_phys(b);
+    }
+    unsigned b = g;
+#pragma unroll
+    for (int a = 0; a < NPOS; a++) b = ins0u(b, p[a]);
+    return b;
+}
+
+template <bool SWZ>
+__device__ __forceinline__ unsigned member_delta(int pos)
+{
+    return SWZ ? herm_phys(1u << pos) : 1u << pos;
+}
+
 // Two-qubit phase on every 16-member group, y_e = sum_f S[e][f] x_f, input-stationary: each
 // thread keeps its group's 16 outputs as 8 packed pairs (Re y_2p, Re y_2p+1) and
 // (Im y_2p, Im y_2p+1), streams the 16 inputs once, and for every input and output pair
 // issues four packed FMAs against one 16-byte coefficient load:
 //   Re += A (xr, xr) + B (-xi, -xi),   Im += A (xi, xi) + B (xr, xr).
 // G groups per thread share each coefficient load.
-template <int G, int NT = kTileThreads, bool UNROLL = true>
+// Member offsets combine by XOR: without the swizzle they are disjoint bits, with it the
+// map is linear.
+template <int G, int NT = kTileThreads, bool UNROLL = true, bool SWZ = false>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
 {
-    const unsigned d0 = 1u << F.pos[0], d1 = 1u << F.pos[1], d2 = 1u << F.pos[2], d3 = 1u << F.pos[3];
+    const unsigned d0 = member_delta<SWZ>(F.pos[0]), d1 = member_delta<SWZ>(F.pos[1]),
+                   d2 = member_delta<SWZ>(F.pos[2]), d3 = member_delta<SWZ>(F.pos[3]);
     int p[4] = {F.pos[0], F.pos[1], F.pos[2], F.pos[3]};
 #pragma unroll
     for (int a = 0; a < 4; a++)
@@ -91,7 +120,7 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
     for (unsigned g0 = threadIdx.x; g0 < ng; g0 += G * NT) {
         unsigned base[G];
 #pragma unroll
-        for (int j = 0; j < G; j++) base[j] = ins0u(ins0u(ins0u(ins0u(g0 + j * NT, p[0]), p[1]), p[2]), p[3]);
+        for (int j = 0; j < G; j++) base[j] = group_base<SWZ>(g0 + j * NT, F, p, TB - 4);
         unsigned long long R[G][8], I[G][8];
 #pragma unroll
         for (int j = 0; j < G; j++)
@@ -111,11 +140,11 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
     }
 #pragma unroll(UNROLL ? 16 : 1)
         for (int f = 0; f < 16; f++) {
-            const unsigned of = ((f & 8) ? d0 : 0u) + ((f & 4) ? d1 : 0u) + ((f & 2) ? d2 : 0u) + ((f & 1) ? d3 : 0u);
+            const unsigned of = ((f & 8) ? d0 : 0u) ^ ((f & 4) ? d1 : 0u) ^ ((f & 2) ? d2 : 0u) ^ ((f & 1) ? d3 : 0u);
             unsigned long long xrr[G], xii[G], nxi[G];
 #pragma unroll
             for (int j = 0; j < G; j++) {
-                const float2 v = tile[base[j] + of];
+                const float2 v = tile[base[j] ^ of];
                 xrr[j] = pack2(v.x, v.x);
                 xii[j] = pack2(v.y, v.y);
                 nxi[j] = pack2(-v.y, -v.y);
@@ -131,29 +160,29 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
 #pragma unroll
             for (int q = 0; q < 8; q++) {
                 const float2 re = unpack2(R[j][q]), im = unpack2(I[j][q]);
-                const int e0 = 2 * q, e1 = 2 * q + 1;
-                tile[base[j] + ((e0 & 8) ? d0 : 0u) + ((e0 & 4) ? d1 : 0u) + ((e0 & 2) ? d2 : 0u)] = make_float2(re.x, im.x);
-                tile[base[j] + ((e1 & 8) ? d0 : 0u) + ((e1 & 4) ? d1 : 0u) + ((e1 & 2) ? d2 : 0u) + d3] =
-                    make_float2(re.y, im.y);
+                const int e0 = 2 * q;  // e0 + 1 differs in the d3 member bit
+                const unsigned o0 = base[j] ^ ((e0 & 8) ? d0 : 0u) ^ ((e0 & 4) ? d1 : 0u) ^ ((e0 & 2) ? d2 : 0u);
+                tile[o0] = make_float2(re.x, im.x);
+                tile[o0 ^ d3] = make_float2(re.y, im.y);
             }
     }
 }
 
 // One-qubit phase: 4x4 superoperator on every (row pair x column pair) group.
-template <int NT = kTileThreads>
+template <int NT = kTileThreads, bool SWZ = false>
 __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
 {
     const int pr = F.pos[0], pc = F.pos[1];
-    const int lo = pr < pc ? pr : pc, hi = pr < pc ? pc : pr;
-    const unsigned dr = 1u << pr, dc = 1u << pc;
+    const int p[2] = {pr < pc ? pr : pc, pr < pc ? pc : pr};
+    const unsigned dr = member_delta<SWZ>(pr), dc = member_delta<SWZ>(pc);
     float2 s[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) s[i] = S[i];
     const unsigned ng = 1u << (TB - 2);
     for (unsigned g = threadIdx.x; g < ng; g += NT) {
-        unsigned b = ins0u(ins0u(g, lo), hi);
-        float2 x[4] = {tile[b], tile[b + dc], tile[b + dr], tile[b + dr + dc]};
+        const unsigned b = group_base<SWZ>(g, F, p, TB - 2);
+        float2 x[4] = {tile[b], tile[b ^ dc], tile[b ^ dr], tile[b ^ dr ^ dc]};
         float2 y[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
@@ -162,9 +191,9 @@ __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, c
             for (int f = 0; f < 4; f++) cfma(y[e], s[4 * e + f], x[f]);
         }
         tile[b] = y[0];
-        tile[b + dc] = y[1];
-        tile[b + dr] = y[2];
-        tile[b + dr + dc] = y[3];
+        tile[b ^ dc] = y[1];
+        tile[b ^ dr] = y[2];
+        tile[b ^ dr ^ dc] = y[3];
     }
 }
 
@@ -190,11 +219,12 @@ __device__ __forceinline__ void quartet4(const float2 (&s)[16], float2 (&x)[16],
 // Product phase: two one-qubit superoperators (S_a on (r_a, c_a), then S_b on (r_b, c_b);
 // they commute) on every 16-member group, in one shared-memory round trip.  Member
 // index e = 8 r_a + 4 r_b + 2 c_a + c_b.
-template <int NT = kTileThreads>
+template <int NT = kTileThreads, bool SWZ = false>
 __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int TB, const FPhase &F,
                                                 const float2 *__restrict__ S)
 {
-    const unsigned d0 = 1u << F.pos[0], d1 = 1u << F.pos[1], d2 = 1u << F.pos[2], d3 = 1u << F.pos[3];
+    const unsigned d0 = member_delta<SWZ>(F.pos[0]), d1 = member_delta<SWZ>(F.pos[1]),
+                   d2 = member_delta<SWZ>(F.pos[2]), d3 = member_delta<SWZ>(F.pos[3]);
     int p[4] = {F.pos[0], F.pos[1], F.pos[2], F.pos[3]};
 #pragma unroll
     for (int a = 0; a < 4; a++)
@@ -203,11 +233,11 @@ __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int T
             if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
     const unsigned ng = 1u << (TB - 4);
     for (unsigned g = threadIdx.x; g < ng; g += NT) {
-        const unsigned base = ins0u(ins0u(ins0u(ins0u(g, p[0]), p[1]), p[2]), p[3]);
+        const unsigned base = group_base<SWZ>(g, F, p, TB - 4);
         float2 x[16];
 #pragma unroll
         for (int e = 0; e < 16; e++)
-            x[e] = tile[base + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u)];
+            x[e] = tile[base ^ ((e & 8) ? d0 : 0u) ^ ((e & 4) ? d1 : 0u) ^ ((e & 2) ? d2 : 0u) ^ ((e & 1) ? d3 : 0u)];
         float2 s[16];
 #pragma unroll
         for (int i = 0; i < 16; i++) s[i] = S[i];
@@ -225,23 +255,23 @@ __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int T
         }
 #pragma unroll
         for (int e = 0; e < 16; e++)
-            tile[base + ((e & 8) ? d0 : 0u) + ((e & 4) ? d1 : 0u) + ((e & 2) ? d2 : 0u) + ((e & 1) ? d3 : 0u)] = x[e];
+            tile[base ^ ((e & 8) ? d0 : 0u) ^ ((e & 4) ? d1 : 0u) ^ ((e & 2) ? d2 : 0u) ^ ((e & 1) ? d3 : 0u)] = x[e];
     }
 }
 
 // Apply one phase whose coefficients are at S (shared or global memory).
-template <int NT = kTileThreads, bool UNROLL = true>
+template <int NT = kTileThreads, bool UNROLL = true, bool SWZ = false>
 __device__ __forceinline__ void tile_apply_phase(float2 *__restrict__ tile, int TB, const FPhase &F,
                                                  const float2 *__restrict__ S)
 {
     if (F.nq == PH_TWO) {
         constexpr int kLogNT = NT == 128 ? 7 : NT == 256 ? 8 : NT == 512 ? 9 : 10;
-        if (TB - 4 >= kLogNT + 1) tile_phase2<2, NT, UNROLL>(tile, TB, F, S);  // >= 2 groups per thread
-        else tile_phase2<1, NT, UNROLL>(tile, TB, F, S);
+        if (TB - 4 >= kLogNT + 1) tile_phase2<2, NT, UNROLL, SWZ>(tile, TB, F, S);  // >= 2 groups per thread
+        else tile_phase2<1, NT, UNROLL, SWZ>(tile, TB, F, S);
     } else if (F.nq == PH_PRODUCT) {
-        tile_phase_prod<NT>(tile, TB, F, S);
+        tile_phase_prod<NT, SWZ>(tile, TB, F, S);
     } else {
-        tile_phase1<NT>(tile, TB, F, S);
+        tile_phase1<NT, SWZ>(tile, TB, F, S);
     }
 }
 
@@ -328,7 +358,7 @@ __device__ __forceinline__ void tile_phases(const FPass &P, const FPhase *__rest
     }
 }
 
-template <int NT>
+template <int NT, bool SWZ = false>
 __device__ __forceinline__ void tile_store_nt(float2 *__restrict__ rho, const FPass &P, uint64_t t,
                                               const float2 *__restrict__ tile, const uint64_t *__restrict__ hoff)
 {
@@ -339,7 +369,7 @@ __device__ __forceinline__ void tile_store_nt(float2 *__restrict__ rho, const FP
     const float4 *t4 = reinterpret_cast<const float4 *>(tile);
     for (unsigned v = threadIdx.x; v < nvec; v += NT) {
         unsigned e = 2 * v;
-        *reinterpret_cast<float4 *>(rho + base + hoff[e >> L] + (e & lmask)) = t4[v];
+        *reinterpret_cast<float4 *>(rho + base + hoff[e >> L] + (e & lmask)) = t4[SWZ ? herm_phys(e) >> 1 : v];
     }
 }
 
@@ -365,6 +395,66 @@ __device__ __forceinline__ void tile_process(float2 *__restrict__ rho, const FPa
     tile_load(rho, P, t, sm, init);
     tile_phases(P, phases, coefs, sm);
     tile_store(rho, P, t, sm);
+}
+
+// ------------------------------------------------------------------ mbarriers (CTA scope)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Arrive on `bar` once every cp.async this thread issued before has landed (the barrier's
+// expected count includes this arrival).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` of `bar` to complete, giving up after `limit` polls
+// (each failed poll also sleeps ~256 ns); returns whether the phase completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit)
+{
+    for (unsigned it = 0;; it++) {
+        if (mbar_test(bar, parity)) return true;
+        if (it >= limit) return false;
+        __nanosleep(256);
+    }
+}
+
+// AND of `pred` over the `count` threads that take part in named barrier `id` (also a
+// barrier among them).
+__device__ __forceinline__ bool bar_and(int id, int count, bool pred)
+{
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)pred), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
 }
 
 }  // namespace qcw

@@ -32,8 +32,24 @@ struct FPhase {
     int nq;            // PH_ONE (4x4), PH_TWO (16x16) or PH_PRODUCT (two 4x4: S_a then S_b)
     int coef;          // offset of the superoperator(s) in the coefficient array (float2 units)
     int8_t pos[4];     // tile positions of (r_a, r_b, c_a, c_b); (r_a, c_a) for PH_ONE
-    int pad;
+    int8_t opos[12];   // Hermitian passes: the tile bits outside the phase, in the order the
+                       // group index enumerates them (the first five vary across a warp)
+    int pad[2];
 };
+
+// Shared-memory position of tile element e in a Hermitian pass: bits 1..3 of e are XORed with
+// a linear function of bits 4..11, bit 0 and bits 4.. are kept, so 16-byte pairs stay whole.
+// A Hermitian tile of six qubits has the column bit of tile qubit j at bit j and its row bit
+// at bit j + 6; each of bits 1, 2, 3 is mixed with bits of two more qubits (bit 1 with 5, 9;
+// bit 2 with 6, 10; bit 3 with 4, 7, 8, 11), so a phase on one or two qubits always leaves
+// outside bits whose positions span bits 1..3 mod 16: the warp's groups then fall on distinct
+// bank pairs.
+__host__ __device__ inline unsigned herm_phys(unsigned e)
+{
+    const unsigned t = e >> 4, s = t ^ (t >> 4);
+    const unsigned sw = ((s >> 1) & 3u) | (((s ^ (s >> 3)) & 1u) << 2);
+    return e ^ (sw << 1);
+}
 
 // Coefficients of a phase kind, in float2 units.  A two-qubit superoperator S (16 x 16
 // complex) is stored for packed FP32 arithmetic: for input f and output pair p (outputs 2p,

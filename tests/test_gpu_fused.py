@@ -198,13 +198,14 @@ def test_persistent_pipeline_matches_plain_n12(q):
     assert np.abs(a - f).max() <= 1e-6
 
 
-@pytest.mark.parametrize("n", [8, 11])
+@pytest.mark.parametrize("n", [6, 8, 11])
 def test_hermitian_kernel_matches_general_kernels(q, n):
-    """The Hermitian pass kernel (tiles on or above the diagonal, mirrors written as conjugate
-    transposes) against the general per-tile kernel and, at n = 8, the oracle."""
+    """The Hermitian pass kernels (tiles on or above the diagonal, mirrors written as conjugate
+    transposes; one CTA per tile pair, and the warp-specialised persistent one) against the
+    general per-tile kernel and, at n = 6 and 8, the oracle."""
     c = wl.random_circuit(n, 80, 808 + n, "mixed", "adpd")
     got = {}
-    for which in (1, 2):
+    for which in (1, 2, 3):
         d = q.Density(n)
         d.set_mode(q.QCW_MODE_FUSED, 5)
         d.set_fused_kernel(which)
@@ -214,8 +215,10 @@ def test_hermitian_kernel_matches_general_kernels(q, n):
         d.close()
     assert np.abs(got[2] - got[1]).max() <= 1e-6
     assert np.abs(got[2] - got[2].conj().T).max() <= 1e-7
-    if n == 8:
-        assert np.abs(got[2] - oracle.run_circuit(c)).max() <= ATOL
+    # same tile layout and phase arithmetic: the two Hermitian kernels agree bit for bit
+    np.testing.assert_array_equal(got[3], got[2])
+    if n <= 8:
+        assert np.abs(got[3] - oracle.run_circuit(c)).max() <= ATOL
 
 
 @pytest.mark.parametrize("k", [4, 5])
@@ -224,7 +227,7 @@ def test_hermitian_kernel_at_n12(q, k):
     general per-tile kernel."""
     c = wl.random_circuit(12, 60, 1200 + k, "mixed", "adpd")
     got = {}
-    for w in (1, 2):
+    for w in (1, 2, 3):
         d = q.Density(12)
         d.set_mode(q.QCW_MODE_FUSED, k)
         d.set_fused_kernel(w)
@@ -233,3 +236,29 @@ def test_hermitian_kernel_at_n12(q, k):
         got[w] = d.get_state()
         d.close()
     assert np.abs(got[2] - got[1]).max() <= 1e-6
+    np.testing.assert_array_equal(got[3], got[2])
+
+
+def test_warp_specialised_wait_runs_out_and_context_recovers(q):
+    """The first CTA skips the load of its first tile: its consumers' bounded wait runs out,
+    the producer's wait for them runs out next, the kernel ends and the following readout
+    reports QCW_ETIMEOUT (sticky until reset).  After a reset the context works again."""
+    n = 9
+    c = wl.random_circuit(n, 40, 4040, "mixed", "adpd")
+    d = q.Density(n)
+    d.set_mode(q.QCW_MODE_FUSED, 4)
+    d.set_fused_kernel(3)
+    d.set_fused_wait_limit(2000, 0)
+    for op in c.ops:
+        d.apply_op(op)
+    for _ in range(2):
+        with pytest.raises(q.QcwError) as e:
+            d.trace()
+        assert e.value.status == q.QCW_ETIMEOUT
+    d.set_fused_wait_limit(0, -1)
+    d.reset()
+    for op in c.ops:
+        d.apply_op(op)
+    d.sync()
+    assert np.abs(d.get_state() - oracle.run_circuit(c)).max() <= ATOL
+    d.close()
