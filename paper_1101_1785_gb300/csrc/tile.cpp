@@ -46,6 +46,78 @@ static int tile_pos(const FPass &fp, int vbit)
     return -1;
 }
 
+// Two-qubit phases run in a Pauli basis (see tile_phase2).  Per qubit of the phase, with its
+// row and column bits (r, c), the device maps the members (b00, b01, b10, b11) to
+// (I, X, D, Z) = (b00 + b11, b01 + b10, b01 - b10, b00 - b11) and back with
+// (b00, b01, b10, b11) = (I + Z, X + D, X - D, I - Z); I, X, Z and i D are 2x the Pauli
+// coefficients tr(P b) of the 2x2 block.  Member e = 8 r_a + 4 r_b + 2 c_a + c_b keeps its bit
+// positions: Pauli index bits (2 r + c) per qubit.
+static void pauli_fwd(c128 *x)
+{
+    for (int e2 = 0; e2 < 2; e2++)
+        for (int e0 = 0; e0 < 2; e0++) {
+            const int i = 4 * e2 + e0;
+            const c128 b00 = x[i], b01 = x[i + 2], b10 = x[i + 8], b11 = x[i + 10];
+            x[i] = b00 + b11, x[i + 2] = b01 + b10, x[i + 8] = b01 - b10, x[i + 10] = b00 - b11;
+        }
+    for (int e3 = 0; e3 < 2; e3++)
+        for (int e1 = 0; e1 < 2; e1++) {
+            const int i = 8 * e3 + 2 * e1;
+            const c128 b00 = x[i], b01 = x[i + 1], b10 = x[i + 4], b11 = x[i + 5];
+            x[i] = b00 + b11, x[i + 1] = b01 + b10, x[i + 4] = b01 - b10, x[i + 5] = b00 - b11;
+        }
+}
+
+static void pauli_inv(c128 *w)
+{
+    for (int e3 = 0; e3 < 2; e3++)
+        for (int e1 = 0; e1 < 2; e1++) {
+            const int i = 8 * e3 + 2 * e1;
+            const c128 I = w[i], X = w[i + 1], D = w[i + 4], Z = w[i + 5];
+            w[i] = I + Z, w[i + 1] = X + D, w[i + 4] = X - D, w[i + 5] = I - Z;
+        }
+    for (int e2 = 0; e2 < 2; e2++)
+        for (int e0 = 0; e0 < 2; e0++) {
+            const int i = 4 * e2 + e0;
+            const c128 I = w[i], X = w[i + 2], D = w[i + 8], Z = w[i + 10];
+            w[i] = I + Z, w[i + 2] = X + D, w[i + 8] = X - D, w[i + 10] = I - Z;
+        }
+}
+
+// Pauli index with an odd number of D components: there the Pauli coefficient is i D.
+static bool pauli_odd(int e) { return (((e >> 3) & 1) && !((e >> 1) & 1)) != (((e >> 2) & 1) && !(e & 1)); }
+
+// Real transfer matrix R of a two-qubit superoperator S (16 x 16, S[e][f], row-major) for the
+// device's order of operations: u = fwd(x); v_f = i u_f on odd indices (u_f elsewhere);
+// c = R v; w_e = -i c_e on odd indices (c_e elsewhere); x' = inv(w) = S x.  Since
+// inv(fwd(x)) = 4 x, R = (1/16) d fwd(S inv(.)) conj(d) with d = i on odd indices.  R is real
+// because S preserves Hermiticity (every gate and channel does): in the Hermitian Pauli basis
+// its matrix is real, and the d factors turn D into the Y coefficient.
+static void pauli_transfer(const std::vector<c128> &S, double R[16][16])
+{
+    c128 M[16][16];
+    for (int f = 0; f < 16; f++) {
+        c128 col[16] = {};
+        col[f] = 1.0;
+        pauli_inv(col);  // column f of inv
+        c128 sc[16];
+        for (int e = 0; e < 16; e++) {
+            c128 acc = 0;
+            for (int g = 0; g < 16; g++) acc += S[(size_t)e * 16 + g] * col[g];
+            sc[e] = acc;
+        }
+        pauli_fwd(sc);
+        for (int e = 0; e < 16; e++) M[e][f] = sc[e];
+    }
+    for (int e = 0; e < 16; e++)
+        for (int f = 0; f < 16; f++) {
+            c128 z = M[e][f] / 16.0;
+            if (pauli_odd(e)) z *= c128(0, 1);
+            if (pauli_odd(f)) z *= c128(0, -1);
+            R[e][f] = z.real();
+        }
+}
+
 // Hermitian passes: enumeration order of the tile bits outside a phase (positions pos[0..np)).
 // The first bits are the ones whose shared-memory bank pairs (bits 0..3 of herm_phys) are
 // linearly independent, so that the 32 groups a warp handles at once spread over all 16
@@ -99,12 +171,11 @@ void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TileP
             if (ph.S.empty()) {
                 // structure-only plan (width search): no coefficients
             } else if (f.nq == PH_TWO) {
+                double R[16][16];
+                pauli_transfer(ph.S, R);
                 for (int in = 0; in < 16; in++)
-                    for (int pr = 0; pr < 8; pr++) {
-                        const c128 a = ph.S[(size_t)(2 * pr) * 16 + in], b = ph.S[(size_t)(2 * pr + 1) * 16 + in];
-                        out.coefs.push_back(make_float2((float)a.real(), (float)b.real()));
-                        out.coefs.push_back(make_float2((float)a.imag(), (float)b.imag()));
-                    }
+                    for (int pr = 0; pr < 8; pr++)
+                        out.coefs.push_back(make_float2((float)R[2 * pr][in], (float)R[2 * pr + 1][in]));
             } else {
                 for (const c128 &z : ph.S) out.coefs.push_back(make_float2((float)z.real(), (float)z.imag()));
             }

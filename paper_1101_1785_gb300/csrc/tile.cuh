@@ -95,15 +95,50 @@ __device__ __forceinline__ unsigned member_delta(int pos)
     return SWZ ? herm_phys(1u << pos) : 1u << pos;
 }
 
-// Two-qubit phase on every 16-member group, y_e = sum_f S[e][f] x_f, input-stationary: each
-// thread keeps its group's 16 outputs as 8 packed pairs (Re y_2p, Re y_2p+1) and
-// (Im y_2p, Im y_2p+1), streams the 16 inputs once, and for every input and output pair
-// issues four packed FMAs against one 16-byte coefficient load:
-//   Re += A (xr, xr) + B (-xi, -xi),   Im += A (xi, xi) + B (xr, xr).
-// G groups per thread share each coefficient load.
-// Member offsets combine by XOR: without the swizzle they are disjoint bits, with it the
-// map is linear.
-template <int G, int NT = kTileThreads, bool UNROLL = true, bool SWZ = false>
+__device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;\n" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Pauli index (two bits per qubit, as the member index) with an odd number of D components.
+__host__ __device__ constexpr bool pauli_odd_idx(int e)
+{
+    return (((e >> 3) & 1) && !((e >> 1) & 1)) != (((e >> 2) & 1) && !(e & 1));
+}
+
+// Butterflies on one qubit of a 16-member group (packed complex), in place: the members
+// (b00, b01, b10, b11) of the qubit's (row, column) bits at offsets (0, S2, S1, S1 + S2) from
+// O become (b00 + b11, b01 + b10, b01 - b10, b00 - b11) = (I, X, D, Z).  Applied twice this
+// gives 2x the input, so the same butterflies also return from (I, X, D, Z).
+template <int S1, int S2, int O>
+__device__ __forceinline__ void pauli_quad(unsigned long long (&x)[16])
+{
+    const unsigned long long a = x[O], b = x[O + S2], c = x[O + S1], d = x[O + S1 + S2];
+    x[O] = fadd2(a, d);
+    x[O + S2] = fadd2(b, c);
+    x[O + S1] = fsub2(b, c);
+    x[O + S1 + S2] = fsub2(a, d);
+}
+
+// Both qubits of a two-qubit phase: qubit a on bits (e3, e1), qubit b on bits (e2, e0).
+__device__ __forceinline__ void pauli_butterflies(unsigned long long (&x)[16])
+{
+    pauli_quad<8, 2, 0>(x), pauli_quad<8, 2, 1>(x), pauli_quad<8, 2, 4>(x), pauli_quad<8, 2, 5>(x);
+    pauli_quad<4, 1, 0>(x), pauli_quad<4, 1, 2>(x), pauli_quad<4, 1, 8>(x), pauli_quad<4, 1, 10>(x);
+}
+
+// Two-qubit phase on every 16-member group (the row quartet x column quartet of Sec. 3.2 for
+// the phase's qubits), x' = S x, computed in the Pauli basis of the two qubits: forward
+// butterflies (additions only), v = the Pauli coefficients (i on the members with an odd
+// number of D components), c = R v with R the real transfer matrix (one packed FMA per
+// coefficient: R[e][f] times the real and imaginary parts of v_f, two outputs per register
+// pair), back to the butterfly basis (-i on the odd members) and inverse butterflies.  Half
+// the multiply-adds of the complex 16 x 16 product, and half the coefficient bytes.
+// Member offsets combine by XOR: without the swizzle they are disjoint bits, with it the map
+// is linear.
+template <int NT = kTileThreads, bool UNROLL = true, bool SWZ = false>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
 {
@@ -117,54 +152,47 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
             if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
     const unsigned ng = 1u << (TB - 4);
     const unsigned sbase = smem_u32(S);
-    for (unsigned g0 = threadIdx.x; g0 < ng; g0 += G * NT) {
-        unsigned base[G];
+    unsigned long long *t64 = reinterpret_cast<unsigned long long *>(tile);
+    for (unsigned g = threadIdx.x; g < ng; g += NT) {
+        const unsigned base = group_base<SWZ>(g, F, p, TB - 4);
+        unsigned off[16];
 #pragma unroll
-        for (int j = 0; j < G; j++) base[j] = group_base<SWZ>(g0 + j * NT, F, p, TB - 4);
-        unsigned long long R[G][8], I[G][8];
+        for (int e = 0; e < 16; e++)
+            off[e] = base ^ ((e & 8) ? d0 : 0u) ^ ((e & 4) ? d1 : 0u) ^ ((e & 2) ? d2 : 0u) ^ ((e & 1) ? d3 : 0u);
+        unsigned long long x[16];
 #pragma unroll
-        for (int j = 0; j < G; j++)
+        for (int e = 0; e < 16; e++) x[e] = t64[off[e]];
+        pauli_butterflies(x);
+        unsigned long long R[8], I[8];
 #pragma unroll
-            for (int q = 0; q < 8; q++) R[j][q] = I[j][q] = 0ull;
-#define QCW_PHASE2_PAIR(Q)                                                   \
-    {                                                                        \
-        unsigned long long A, B;                                             \
-        lds_coef<16 * (Q)>(sf, A, B);                                        \
-        _Pragma("unroll") for (int j = 0; j < G; j++)                        \
-        {                                                                    \
-            R[j][(Q)] = ffma2(A, xrr[j], R[j][(Q)]);                         \
-            R[j][(Q)] = ffma2(B, nxi[j], R[j][(Q)]);                         \
-            I[j][(Q)] = ffma2(A, xii[j], I[j][(Q)]);                         \
-            I[j][(Q)] = ffma2(B, xrr[j], I[j][(Q)]);                         \
-        }                                                                    \
-    }
-#pragma unroll(UNROLL ? 16 : 1)
+        for (int q = 0; q < 8; q++) R[q] = I[q] = 0ull;
+#pragma unroll
         for (int f = 0; f < 16; f++) {
-            const unsigned of = ((f & 8) ? d0 : 0u) ^ ((f & 4) ? d1 : 0u) ^ ((f & 2) ? d2 : 0u) ^ ((f & 1) ? d3 : 0u);
-            unsigned long long xrr[G], xii[G], nxi[G];
-#pragma unroll
-            for (int j = 0; j < G; j++) {
-                const float2 v = tile[base[j] ^ of];
-                xrr[j] = pack2(v.x, v.x);
-                xii[j] = pack2(v.y, v.y);
-                nxi[j] = pack2(-v.y, -v.y);
-            }
-            const unsigned sf = sbase + 128u * (unsigned)f;  // input f: 8 pairs x 16 bytes
-            QCW_PHASE2_PAIR(0) QCW_PHASE2_PAIR(1) QCW_PHASE2_PAIR(2) QCW_PHASE2_PAIR(3)
-            QCW_PHASE2_PAIR(4) QCW_PHASE2_PAIR(5) QCW_PHASE2_PAIR(6) QCW_PHASE2_PAIR(7)
+            const float2 u = unpack2(x[f]);
+            const unsigned long long xr = pauli_odd_idx(f) ? pack2(-u.y, -u.y) : pack2(u.x, u.x);
+            const unsigned long long xi = pauli_odd_idx(f) ? pack2(u.x, u.x) : pack2(u.y, u.y);
+            const unsigned sf = sbase + 64u * (unsigned)f;  // input f: 8 pairs x 8 bytes
+#define QCW_PAULI_PAIRS(Q)                         \
+    {                                              \
+        unsigned long long A, B;                   \
+        lds_coef<8 * (Q)>(sf, A, B);               \
+        R[(Q)] = ffma2(A, xr, R[(Q)]);             \
+        I[(Q)] = ffma2(A, xi, I[(Q)]);             \
+        R[(Q) + 1] = ffma2(B, xr, R[(Q) + 1]);     \
+        I[(Q) + 1] = ffma2(B, xi, I[(Q) + 1]);     \
+    }
+            QCW_PAULI_PAIRS(0) QCW_PAULI_PAIRS(2) QCW_PAULI_PAIRS(4) QCW_PAULI_PAIRS(6)
+#undef QCW_PAULI_PAIRS
         }
-#undef QCW_PHASE2_PAIR
-        // every input of the group has been read: write the outputs in place
 #pragma unroll
-        for (int j = 0; j < G; j++)
+        for (int q = 0; q < 8; q++) {
+            const float2 re = unpack2(R[q]), im = unpack2(I[q]);
+            x[2 * q] = pauli_odd_idx(2 * q) ? pack2(im.x, -re.x) : pack2(re.x, im.x);
+            x[2 * q + 1] = pauli_odd_idx(2 * q + 1) ? pack2(im.y, -re.y) : pack2(re.y, im.y);
+        }
+        pauli_butterflies(x);
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const float2 re = unpack2(R[j][q]), im = unpack2(I[j][q]);
-                const int e0 = 2 * q;  // e0 + 1 differs in the d3 member bit
-                const unsigned o0 = base[j] ^ ((e0 & 8) ? d0 : 0u) ^ ((e0 & 4) ? d1 : 0u) ^ ((e0 & 2) ? d2 : 0u);
-                tile[o0] = make_float2(re.x, im.x);
-                tile[o0 ^ d3] = make_float2(re.y, im.y);
-            }
+        for (int e = 0; e < 16; e++) t64[off[e]] = x[e];
     }
 }
 
@@ -265,9 +293,7 @@ __device__ __forceinline__ void tile_apply_phase(float2 *__restrict__ tile, int 
                                                  const float2 *__restrict__ S)
 {
     if (F.nq == PH_TWO) {
-        constexpr int kLogNT = NT == 128 ? 7 : NT == 256 ? 8 : NT == 512 ? 9 : 10;
-        if (TB - 4 >= kLogNT + 1) tile_phase2<2, NT, UNROLL, SWZ>(tile, TB, F, S);  // >= 2 groups per thread
-        else tile_phase2<1, NT, UNROLL, SWZ>(tile, TB, F, S);
+        tile_phase2<NT, UNROLL, SWZ>(tile, TB, F, S);
     } else if (F.nq == PH_PRODUCT) {
         tile_phase_prod<NT, SWZ>(tile, TB, F, S);
     } else {

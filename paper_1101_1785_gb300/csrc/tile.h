@@ -51,11 +51,12 @@ __host__ __device__ inline unsigned herm_phys(unsigned e)
     return e ^ (sw << 1);
 }
 
-// Coefficients of a phase kind, in float2 units.  A two-qubit superoperator S (16 x 16
-// complex) is stored for packed FP32 arithmetic: for input f and output pair p (outputs 2p,
-// 2p+1) the 16 bytes (Re S[2p][f], Re S[2p+1][f], Im S[2p][f], Im S[2p+1][f]), f-major
-// (256 float2).  One- and product phases store their 4x4 matrices row-major.
-__host__ __device__ inline int phase_coefs(int nq) { return nq == PH_TWO ? 256 : nq == PH_PRODUCT ? 32 : 16; }
+// Coefficients of a phase kind, in float2 units.  A two-qubit phase stores the real 16 x 16
+// transfer matrix R of its superoperator in the Pauli basis of the two qubits, for packed FP32
+// arithmetic: for input f and output pair p (outputs 2p, 2p+1) the pair (R[2p][f],
+// R[2p+1][f]), f-major (128 float2).  One- and product phases store their complex 4x4
+// superoperators row-major.
+__host__ __device__ inline int phase_coefs(int nq) { return nq == PH_TWO ? 128 : nq == PH_PRODUCT ? 32 : 16; }
 
 constexpr int kTileThreads = 256;  // threads per CTA of the tile kernels
 constexpr int kTileBitsMax = 14;   // largest tile: 2^14 complex64 = 128 KiB
