@@ -141,6 +141,33 @@ __device__ __forceinline__ void pair_of(unsigned p, unsigned &o_r, unsigned &o_c
     o_r = (unsigned)(pp - c * (c + 1) / 2);
 }
 
+// Pair p -> (lo, hi), lo <= hi < M, in 4 x 4 blocks of the triangle: block rows R (pairs before
+// row R: 8 R^2 + 2 R), in each the off-diagonal blocks (16 pairs, lo fastest) and then the
+// diagonal block (10 pairs, triangle order).  Pairs that run side by side then cover four
+// consecutive lo and four consecutive hi values, so both the evolved tiles (outside column
+// bits lo) and their mirrors (outside column bits hi) fill whole cache lines together.
+__device__ __forceinline__ void pair_blocked(unsigned p, unsigned M, unsigned &lo, unsigned &hi)
+{
+    if (M < 4) {
+        pair_of(p, lo, hi);
+        return;
+    }
+    const unsigned long long pp = p;
+    unsigned long long R = (unsigned long long)((sqrtf(4.0f + 32.0f * (float)p) - 2.0f) * 0.0625f);
+    while (8 * (R + 1) * (R + 1) + 2 * (R + 1) <= pp) R++;
+    while (8 * R * R + 2 * R > pp) R--;
+    const unsigned q = (unsigned)(pp - (8 * R * R + 2 * R)), r4 = 4 * (unsigned)R;
+    if (q < 16 * (unsigned)R) {
+        hi = r4 + ((q & 15u) >> 2);
+        lo = 4 * (q >> 4) + (q & 3u);
+    } else {
+        unsigned c, r;
+        pair_of(q - 16 * (unsigned)R, c, r);
+        hi = r4 + r;
+        lo = r4 + c;
+    }
+}
+
 constexpr int HT = 128;  // threads of the Hermitian kernel: 2^12-element tiles give 2 groups each
 
 // Mirror tile: element t' holds conj(tile[swap(t')]), swap exchanging the column half and the
@@ -173,11 +200,11 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
     const int TB = P.TB, L = P.L, m = P.nother / 2;
     const TileSmem sm = tile_smem(smem, TB, L);
     tile_hoff_nt<HT>(P, sm.hoff);
-    // The evolved tile is the one with o_c <= o_r (on or below the diagonal): consecutive CTAs
-    // then differ in the outside column bits, so tiles running side by side read adjacent
-    // contiguous runs of rho.  Outside bits ascend: m column bits (o_c) below m row bits (o_r).
+    // The evolved tile is the one with o_c <= o_r (on or below the diagonal), pairs in the
+    // blocked order of pair_blocked.  Outside bits ascend: m column bits (o_c) below m row
+    // bits (o_r).
     unsigned o_r, o_c;
-    pair_of(blockIdx.x, o_c, o_r);
+    pair_blocked(blockIdx.x, 1u << m, o_c, o_r);
     __syncthreads();
     const uint64_t t_self = ((uint64_t)o_r << m) | o_c;
     {
@@ -204,21 +231,30 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
 }
 
 // ------------------------------------------------------------------ warp-specialised Hermitian pass
-// Persistent CTAs (three per SM) of four consumer warps and one producer warp sharing two tile
-// buffers.  CTA c takes the pairs c, c + grid, c + 2 grid, ...  The producer loads the next
-// pair's lower-triangle tile with cp.async while the consumers evolve the current one, and
-// writes evolved tiles (and their conjugate-transposed mirrors) back while the consumers work
-// on the next, so the pass's HBM traffic overlaps its arithmetic instead of adding to it.
-// Hand-over is by mbarriers: full[b] (the 32 producer lanes' cp.async arrivals) and empty[b]
-// (the 128 consumers' arrivals).  Every wait is bounded: on running out, the side that gave up
-// sets the pass's error word and returns, and the other side then runs out too.
+// Persistent CTAs of kWsConsumerWarps consumer warps and kWsProducerWarps producer warps sharing
+// kWsBuf tile buffers.  CTA c takes the pairs c, c + grid, c + 2 grid, ...  The producer loads pair tiles
+// with cp.async up to kWsBuf - 1 ahead of the consumers and writes evolved tiles (and their
+// conjugate-transposed mirrors) back while the consumers work on later ones, so the pass's
+// HBM traffic overlaps its arithmetic instead of adding to it.  Hand-over is by mbarriers:
+// full[b] (every producer lane's cp.async arrival) and empty[b] (every consumer thread's
+// arrival); the producer warps split each tile's rows k and meet at a named barrier between
+// writing a buffer back and refilling it.  Every wait is bounded: on running out, the side that gave up sets the pass's
+// error word and returns, and the other side then runs out too.
 //
-// Tiles are 2^12 elements (six qubits); the producer's lane covers tile bits 0..5 (an element
-// pair) and its loop index k the bits 6..11, so global offsets and swizzled shared-memory
-// positions split into a per-lane part and a per-k part read from a 64-entry table.
-constexpr int WC = 128;                 // consumer threads
-constexpr int WTH = WC + 32;            // plus the producer warp
-constexpr int kWsCtasPerSm = 3;
+// Tiles are 2^12 elements (six qubits); a producer lane covers tile bits 0..5 (an element
+// pair) and the loop index k the bits 6..11, so global offsets and swizzled shared-memory
+// positions split into a per-lane part and a per-k part read from a 64-entry table.  The
+// pass's phase headers and coefficients are copied to shared memory once per CTA when they
+// fit (else each phase's coefficients are staged before it runs).
+constexpr int kWsBuf = 3;
+constexpr int kWsConsumerWarps = 4;
+constexpr int kWsProducerWarps = 2;
+constexpr int kWsCtasPerSm = 2;
+constexpr int WC = 32 * kWsConsumerWarps;  // consumer threads
+constexpr int WP = 32 * kWsProducerWarps;  // producer threads
+constexpr int WTH = WC + WP;
+constexpr int kWsMaxPhases = 24;
+constexpr int kWsCoefMax = kWsBuf >= 3 ? 1536 : 512;  // float2
 constexpr unsigned kWsWaitLimit = 1u << 21;  // polls (>= 0.5 s with the 256 ns back-off)
 
 struct WsEntry {
@@ -227,9 +263,31 @@ struct WsEntry {
     unsigned pm;             // herm_phys(k)
 };
 
-static size_t ws_smem_bytes()
+struct WsSmem {
+    float2 *buf;      // kWsBuf tiles of 2^12 elements
+    WsEntry *tab;     // 64 entries
+    float2 *coef;     // kWsCoefMax
+    FPhase *ph;       // kWsMaxPhases headers
+    int *coff;        // kWsMaxPhases offsets into coef
+    uint64_t *bars;   // full[kWsBuf], empty[kWsBuf]
+};
+
+__host__ __device__ constexpr size_t ws_smem_bytes()
 {
-    return 2 * (sizeof(float2) << 12) + 64 * sizeof(WsEntry) + 256 * sizeof(float2) + 4 * sizeof(uint64_t);
+    return (size_t)kWsBuf * (sizeof(float2) << 12) + 64 * sizeof(WsEntry) + kWsCoefMax * sizeof(float2) +
+           kWsMaxPhases * sizeof(FPhase) + kWsMaxPhases * sizeof(int) + 2 * kWsBuf * sizeof(uint64_t);
+}
+
+__device__ __forceinline__ WsSmem ws_smem(unsigned char *smem)
+{
+    WsSmem w;
+    w.buf = reinterpret_cast<float2 *>(smem);
+    w.tab = reinterpret_cast<WsEntry *>(w.buf + kWsBuf * 4096);
+    w.coef = reinterpret_cast<float2 *>(w.tab + 64);
+    w.ph = reinterpret_cast<FPhase *>(w.coef + kWsCoefMax);
+    w.coff = reinterpret_cast<int *>(w.ph + kWsMaxPhases);
+    w.bars = reinterpret_cast<uint64_t *>(w.coff + kWsMaxPhases);
+    return w;
 }
 
 __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
@@ -238,62 +296,78 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
                     unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float2 *buf = reinterpret_cast<float2 *>(smem);  // two tiles of 2^12 elements
-    WsEntry *tab = reinterpret_cast<WsEntry *>(buf + 2 * 4096);
-    float2 *S = reinterpret_cast<float2 *>(tab + 64);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(S + 256);  // full0, full1, empty0, empty1
+    const WsSmem sm = ws_smem(smem);
     const FPass &P = passes[pass_idx];
-    const int m = P.nother / 2;
+    const int m = P.nother / 2, nph = P.nphase;
     const unsigned tid = threadIdx.x;
     if (tid < 64) {
         unsigned long long g = 0;
         for (int j = 0; j < 6; j++)
             if ((tid >> j) & 1u) g += 1ull << P.tbits[6 + j];
-        tab[tid].ghi = g;
-        tab[tid].phi = herm_phys(tid << 6);
-        tab[tid].pm = herm_phys(tid);
+        sm.tab[tid].ghi = g;
+        sm.tab[tid].phi = herm_phys(tid << 6);
+        sm.tab[tid].pm = herm_phys(tid);
     }
     if (tid == 0) {
-        mbar_init(&bars[0], 32);
-        mbar_init(&bars[1], 32);
-        mbar_init(&bars[2], WC);
-        mbar_init(&bars[3], WC);
+        for (int b = 0; b < kWsBuf; b++) {
+            mbar_init(&sm.bars[b], WP);
+            mbar_init(&sm.bars[kWsBuf + b], WC);
+        }
+    }
+    // phase headers and coefficients, once per CTA when they fit
+    int total = 0;
+    for (int ph = 0; ph < nph; ph++) total += phase_coefs(phases[P.phase0 + ph].nq);
+    const bool pre = nph <= kWsMaxPhases && total <= kWsCoefMax;
+    if (pre) {
+        int off = 0;
+        for (int ph = 0; ph < nph; ph++) {
+            const FPhase F = phases[P.phase0 + ph];
+            const int nc = phase_coefs(F.nq);
+            if (tid == 0) {
+                sm.ph[ph] = F;
+                sm.coff[ph] = off;
+            }
+            for (int j = tid; j < nc; j += WTH) sm.coef[off + j] = coefs[F.coef + j];
+            off += nc;
+        }
     }
     __syncthreads();
     const unsigned ntile = blockIdx.x < npairs ? (npairs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    if (tid >= WC) {  // ---- producer warp
-        const unsigned lane = tid - WC;
-        unsigned long long glo = 0;  // global offset of element 2 lane of a tile (bits 0..5)
+    if (tid >= WC) {  // ---- producer warps
+        const unsigned lane = tid & 31u, pw = (tid - WC) >> 5;
+        unsigned long long glo = 0;  // global offset of element 2 lane of a tile row (bits 0..5)
         for (int j = 0; j < 6; j++)
             if (((2 * lane) >> j) & 1u) glo += 1ull << P.tbits[j];
         const unsigned plo = herm_phys(2 * lane);
         const unsigned pm0 = herm_phys((2 * lane) << 6), pm1 = herm_phys((2 * lane + 1) << 6);
         auto pair_bases = [&](unsigned i, uint64_t &self, uint64_t &mirror) {
             unsigned o_r, o_c;
-            pair_of(blockIdx.x + i * gridDim.x, o_c, o_r);
+            pair_blocked(blockIdx.x + i * gridDim.x, 1u << m, o_c, o_r);
             self = tile_base(P, ((uint64_t)o_r << m) | o_c) + glo;
             mirror = o_r != o_c ? tile_base(P, ((uint64_t)o_c << m) | o_r) + glo : ~0ull;
         };
         auto load = [&](unsigned i) {
-            float2 *bf = buf + ((i & 1u) << 12);
-            uint64_t sb, mb;
-            pair_bases(i, sb, mb);
-#pragma unroll 8
-            for (int k = 0; k < 64; k++) {
-                const WsEntry t = tab[k];
-                cp_async16(bf + (plo ^ t.phi), rho + sb + t.ghi);
-            }
-            cp_async_mbar_arrive(&bars[i & 1u]);
-        };
-        // the element pair (t, t + 1) of the mirror is conj of tile elements swap(t), swap(t + 1)
-        auto store = [&](unsigned i) {
-            const float2 *bf = buf + ((i & 1u) << 12);
+            float2 *bf = sm.buf + ((i % kWsBuf) << 12);
             uint64_t sb, mb;
             pair_bases(i, sb, mb);
 #pragma unroll 4
-            for (int k = 0; k < 64; k++) {
-                const WsEntry t = tab[k];
+            for (unsigned k = pw; k < 64; k += kWsProducerWarps) {
+                const WsEntry t = sm.tab[k];
+                cp_async16(bf + (plo ^ t.phi), rho + sb + t.ghi);
+            }
+            cp_async_mbar_arrive(&sm.bars[i % kWsBuf]);
+        };
+        // One instruction writes one row of the tile (and one row of the mirror): row-local
+        // writes keep HBM efficient.  The element pair (t, t + 1) of the mirror is conj of tile
+        // elements swap(t), swap(t + 1).
+        auto store = [&](unsigned i) {
+            const float2 *bf = sm.buf + ((i % kWsBuf) << 12);
+            uint64_t sb, mb;
+            pair_bases(i, sb, mb);
+#pragma unroll 4
+            for (unsigned k = pw; k < 64; k += kWsProducerWarps) {
+                const WsEntry t = sm.tab[k];
                 *reinterpret_cast<float4 *>(rho + sb + t.ghi) = *reinterpret_cast<const float4 *>(bf + (plo ^ t.phi));
                 if (mb != ~0ull) {
                     const float2 a = bf[pm0 ^ t.pm], b = bf[pm1 ^ t.pm];
@@ -301,41 +375,50 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
                 }
             }
         };
+        // empty[b] completes once per use of buffer b: tile i is its (i / kWsBuf)-th use.  All
+        // producer threads agree on the outcome (named barrier 2).
+        auto wait_empty = [&](unsigned i) {
+            return bar_and(2, WP, mbar_wait(&sm.bars[kWsBuf + i % kWsBuf], (i / kWsBuf) & 1u, wait_limit));
+        };
         bool ok = true;
         for (unsigned i = 0; i < ntile; i++) {
-            if (i >= 2) {
-                ok = __all_sync(0xffffffffu, mbar_wait(&bars[2 + (i & 1u)], ((i >> 1) - 1) & 1u, wait_limit));
+            if (i >= kWsBuf) {
+                ok = wait_empty(i - kWsBuf);
                 if (!ok) break;
-                store(i - 2);
-                __syncwarp();  // the warp's reads of the buffer precede the new copies into it
+                store(i - kWsBuf);
+                bar_sync(2, WP);  // every producer's reads of the buffer precede the new copies into it
             }
             if (!(blockIdx.x == 0 && (int)i == stall_tile)) load(i);
         }
-        for (unsigned i = ntile >= 2 ? ntile - 2 : 0; ok && i < ntile; i++) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&bars[2 + (i & 1u)], (i >> 1) & 1u, wait_limit));
+        for (unsigned i = ntile >= kWsBuf ? ntile - kWsBuf : 0; ok && i < ntile; i++) {
+            ok = wait_empty(i);
             if (ok) store(i);
         }
         cp_async_wait_all();
-        if (!ok && lane == 0) atomicOr(err, 1ull);
+        if (!ok && tid == WC) atomicOr(err, 1ull);
         return;
     }
 
     // ---- consumer warps: the pass's phases on each tile in turn
     bool ok = true;
     for (unsigned i = 0; i < ntile; i++) {
-        const unsigned b = i & 1u;
-        ok = bar_and(1, WC, mbar_wait(&bars[b], (i >> 1) & 1u, wait_limit));
+        const unsigned b = i % kWsBuf;
+        ok = bar_and(1, WC, mbar_wait(&sm.bars[b], (i / kWsBuf) & 1u, wait_limit));
         if (!ok) break;
-        float2 *tile = buf + (b << 12);
-        for (int ph = 0; ph < P.nphase; ph++) {
-            const FPhase F = phases[P.phase0 + ph];
-            const int ncoef = phase_coefs(F.nq);
-            for (int j = tid; j < ncoef; j += WC) S[j] = coefs[F.coef + j];
-            bar_sync(1, WC);
-            tile_apply_phase<WC, false, true>(tile, 12, F, S);
+        float2 *tile = sm.buf + (b << 12);
+        for (int ph = 0; ph < nph; ph++) {
+            if (pre) {
+                tile_apply_phase<WC, false, true>(tile, 12, sm.ph[ph], sm.coef + sm.coff[ph]);
+            } else {
+                const FPhase F = phases[P.phase0 + ph];
+                const int nc = phase_coefs(F.nq);
+                for (int j = tid; j < nc; j += WC) sm.coef[j] = coefs[F.coef + j];
+                bar_sync(1, WC);
+                tile_apply_phase<WC, false, true>(tile, 12, F, sm.coef);
+            }
             bar_sync(1, WC);
         }
-        mbar_arrive(&bars[2 + b]);
+        mbar_arrive(&sm.bars[kWsBuf + b]);
     }
     if (!ok && tid == 0) atomicOr(err, 2ull);
 }

@@ -138,7 +138,8 @@ __device__ __forceinline__ void pauli_butterflies(unsigned long long (&x)[16])
 // the multiply-adds of the complex 16 x 16 product, and half the coefficient bytes.
 // Member offsets combine by XOR: without the swizzle they are disjoint bits, with it the map
 // is linear.
-template <int NT = kTileThreads, bool UNROLL = true, bool SWZ = false>
+// G groups per thread (g, g + NT, ...) share every coefficient load.
+template <int G, int NT = kTileThreads, bool SWZ = false>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
 {
@@ -153,46 +154,61 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
     const unsigned ng = 1u << (TB - 4);
     const unsigned sbase = smem_u32(S);
     unsigned long long *t64 = reinterpret_cast<unsigned long long *>(tile);
-    for (unsigned g = threadIdx.x; g < ng; g += NT) {
-        const unsigned base = group_base<SWZ>(g, F, p, TB - 4);
-        unsigned off[16];
+    auto member = [&](int e) {
+        return ((e & 8) ? d0 : 0u) ^ ((e & 4) ? d1 : 0u) ^ ((e & 2) ? d2 : 0u) ^ ((e & 1) ? d3 : 0u);
+    };
+    for (unsigned g0 = threadIdx.x; g0 < ng; g0 += G * NT) {
+        unsigned base[G];
+        unsigned long long x[G][16];
 #pragma unroll
-        for (int e = 0; e < 16; e++)
-            off[e] = base ^ ((e & 8) ? d0 : 0u) ^ ((e & 4) ? d1 : 0u) ^ ((e & 2) ? d2 : 0u) ^ ((e & 1) ? d3 : 0u);
-        unsigned long long x[16];
+        for (int j = 0; j < G; j++) {
+            base[j] = group_base<SWZ>(g0 + j * NT, F, p, TB - 4);
 #pragma unroll
-        for (int e = 0; e < 16; e++) x[e] = t64[off[e]];
-        pauli_butterflies(x);
-        unsigned long long R[8], I[8];
+            for (int e = 0; e < 16; e++) x[j][e] = t64[base[j] ^ member(e)];
+            pauli_butterflies(x[j]);
+        }
+        unsigned long long R[G][8], I[G][8];
 #pragma unroll
-        for (int q = 0; q < 8; q++) R[q] = I[q] = 0ull;
+        for (int j = 0; j < G; j++)
+#pragma unroll
+            for (int q = 0; q < 8; q++) R[j][q] = I[j][q] = 0ull;
 #pragma unroll
         for (int f = 0; f < 16; f++) {
-            const float2 u = unpack2(x[f]);
-            const unsigned long long xr = pauli_odd_idx(f) ? pack2(-u.y, -u.y) : pack2(u.x, u.x);
-            const unsigned long long xi = pauli_odd_idx(f) ? pack2(u.x, u.x) : pack2(u.y, u.y);
+            unsigned long long xr[G], xi[G];
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                const float2 u = unpack2(x[j][f]);
+                xr[j] = pauli_odd_idx(f) ? pack2(-u.y, -u.y) : pack2(u.x, u.x);
+                xi[j] = pauli_odd_idx(f) ? pack2(u.x, u.x) : pack2(u.y, u.y);
+            }
             const unsigned sf = sbase + 64u * (unsigned)f;  // input f: 8 pairs x 8 bytes
-#define QCW_PAULI_PAIRS(Q)                         \
-    {                                              \
-        unsigned long long A, B;                   \
-        lds_coef<8 * (Q)>(sf, A, B);               \
-        R[(Q)] = ffma2(A, xr, R[(Q)]);             \
-        I[(Q)] = ffma2(A, xi, I[(Q)]);             \
-        R[(Q) + 1] = ffma2(B, xr, R[(Q) + 1]);     \
-        I[(Q) + 1] = ffma2(B, xi, I[(Q) + 1]);     \
+#define QCW_PAULI_PAIRS(Q)                                 \
+    {                                                      \
+        unsigned long long A, B;                           \
+        lds_coef<8 * (Q)>(sf, A, B);                       \
+        _Pragma("unroll") for (int j = 0; j < G; j++)      \
+        {                                                  \
+            R[j][(Q)] = ffma2(A, xr[j], R[j][(Q)]);        \
+            I[j][(Q)] = ffma2(A, xi[j], I[j][(Q)]);        \
+            R[j][(Q) + 1] = ffma2(B, xr[j], R[j][(Q) + 1]); \
+            I[j][(Q) + 1] = ffma2(B, xi[j], I[j][(Q) + 1]); \
+        }                                                  \
     }
             QCW_PAULI_PAIRS(0) QCW_PAULI_PAIRS(2) QCW_PAULI_PAIRS(4) QCW_PAULI_PAIRS(6)
 #undef QCW_PAULI_PAIRS
         }
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const float2 re = unpack2(R[q]), im = unpack2(I[q]);
-            x[2 * q] = pauli_odd_idx(2 * q) ? pack2(im.x, -re.x) : pack2(re.x, im.x);
-            x[2 * q + 1] = pauli_odd_idx(2 * q + 1) ? pack2(im.y, -re.y) : pack2(re.y, im.y);
-        }
-        pauli_butterflies(x);
+        for (int j = 0; j < G; j++) {
 #pragma unroll
-        for (int e = 0; e < 16; e++) t64[off[e]] = x[e];
+            for (int q = 0; q < 8; q++) {
+                const float2 re = unpack2(R[j][q]), im = unpack2(I[j][q]);
+                x[j][2 * q] = pauli_odd_idx(2 * q) ? pack2(im.x, -re.x) : pack2(re.x, im.x);
+                x[j][2 * q + 1] = pauli_odd_idx(2 * q + 1) ? pack2(im.y, -re.y) : pack2(re.y, im.y);
+            }
+            pauli_butterflies(x[j]);
+#pragma unroll
+            for (int e = 0; e < 16; e++) t64[base[j] ^ member(e)] = x[j][e];
+        }
     }
 }
 
@@ -293,7 +309,7 @@ __device__ __forceinline__ void tile_apply_phase(float2 *__restrict__ tile, int 
                                                  const float2 *__restrict__ S)
 {
     if (F.nq == PH_TWO) {
-        tile_phase2<NT, UNROLL, SWZ>(tile, TB, F, S);
+        tile_phase2<1, NT, SWZ>(tile, TB, F, S);
     } else if (F.nq == PH_PRODUCT) {
         tile_phase_prod<NT, SWZ>(tile, TB, F, S);
     } else {
