@@ -171,7 +171,7 @@ def kernel_hash():
 
 def recorded_traffic():
     """dram bytes per fused-pass launch from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", "k_fused_herm_n14_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "k_fused_herm_ws_n14_traffic.txt")
     try:
         kv = {}
         with open(path) as f:
