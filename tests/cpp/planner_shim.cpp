@@ -76,3 +76,48 @@ extern "C" int planner_count_only_mismatch(int n, int kmax, int nops, const int 
     }
     return bad;
 }
+
+// Tile plan (descriptors and packed coefficients) of ops[0, nops) for an n-qubit register, as
+// the fused kernels receive it.  Per phase: kind (1 one-qubit, 2 two-qubit, 3 product), tile
+// positions (4), coefficient offset; per pass: TB and tile bits (16).  Returns the number of
+// phases, or -1 if an output array is too small.
+#include "tile.h"
+
+extern "C" int tile_plan(int n, int kmax, int herm, int tbmax, int nops, const int *kind, const int *k,
+                         const int *qubits, const double *mats, const long long *mat_off, int max_phases,
+                         int *phase_kind, int *phase_pos, int *phase_coef, int *phase_pass, int max_passes,
+                         int *pass_tb, int *pass_tbits, int max_coefs, float *coefs, int *ncoefs)
+{
+    std::vector<QOp> ops(nops);
+    for (int i = 0; i < nops; i++) {
+        QOp &o = ops[i];
+        o.kind = kind[i];
+        o.k = k[i];
+        o.ncontrols = 0;
+        for (int j = 0; j < o.k; j++) o.qubits[j] = qubits[2 * i + j];
+        const int dim = o.kind == 0 ? (1 << o.k) : (1 << (2 * o.k));
+        o.m.resize((size_t)dim * dim);
+        for (int t = 0; t < dim * dim; t++)
+            o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
+    }
+    TilePlan tp;
+    append_tile_plan(plan_passes(ops, 0, ops.size(), n, kmax), n, tbmax, tp, herm != 0);
+    if ((int)tp.phases.size() > max_phases || (int)tp.passes.size() > max_passes || (int)tp.coefs.size() > max_coefs)
+        return -1;
+    for (size_t p = 0; p < tp.passes.size(); p++) {
+        pass_tb[p] = tp.passes[p].TB;
+        for (int j = 0; j < 16; j++) pass_tbits[16 * p + j] = tp.passes[p].tbits[j];
+        for (int ph = 0; ph < tp.passes[p].nphase; ph++) phase_pass[tp.passes[p].phase0 + ph] = (int)p;
+    }
+    for (size_t i = 0; i < tp.phases.size(); i++) {
+        phase_kind[i] = tp.phases[i].nq;
+        for (int j = 0; j < 4; j++) phase_pos[4 * i + j] = tp.phases[i].pos[j];
+        phase_coef[i] = tp.phases[i].coef;
+    }
+    for (size_t i = 0; i < tp.coefs.size(); i++) {
+        coefs[2 * i] = tp.coefs[i].x;
+        coefs[2 * i + 1] = tp.coefs[i].y;
+    }
+    *ncoefs = (int)tp.coefs.size();
+    return (int)tp.phases.size();
+}

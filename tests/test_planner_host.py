@@ -1,7 +1,12 @@
-"""CPU test of the fusion planner (host code): its passes and composed phase superoperators,
-replayed in order with numpy, must reproduce the oracle applying the original operations in
-order (up to complex128 rounding).  This checks the commutation-based reordering, the phase
-composition and the product-phase split without a GPU."""
+"""CPU tests of the fusion planner and tile-plan packing (host code).
+
+The planner's passes and composed phase superoperators, replayed in order with numpy, must
+reproduce the oracle applying the original operations in order (up to complex128 rounding):
+this checks the commutation-based reordering, the phase composition and the product-phase
+split.  The packed tile plan (what the kernels receive) is replayed with the kernels'
+arithmetic -- Pauli butterflies and the real transfer matrix for two-qubit phases, complex 4 x 4
+for product and one-qubit phases -- against the oracle to FP32 accuracy: this checks the
+transfer-matrix convention and every coefficient layout without a GPU."""
 
 import ctypes
 import os
@@ -29,10 +34,12 @@ def _cuda_include():
 def shim(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("planner") / "libplanner_shim.so")
     subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                           "-I", CSRC, "-I", _cuda_include(), "-o", out, SHIM, os.path.join(CSRC, "planner.cpp")])
+                           "-I", CSRC, "-I", _cuda_include(), "-o", out, SHIM, os.path.join(CSRC, "planner.cpp"),
+                           os.path.join(CSRC, "tile.cpp")])
     lib = ctypes.CDLL(out)
     lib.planner_phases.restype = ctypes.c_int
     lib.planner_count_only_mismatch.restype = ctypes.c_int
+    lib.tile_plan.restype = ctypes.c_int
     return lib
 
 
@@ -169,3 +176,110 @@ def test_count_only_plan_has_the_same_structure(shim, n, kmax):
     bad = shim.planner_count_only_mismatch(n, kmax, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P),
                                            qs.ctypes.data_as(P), mats.ctypes.data_as(P), offs.ctypes.data_as(P))
     assert bad == 0
+
+
+def _tile_plan(shim, n, kmax, herm, tbmax, ops):
+    kinds, ks, qs, mats, offs = _marshal(ops)
+    maxp, maxc = 4 * len(ops) + 8, 256 * (4 * len(ops) + 8)
+    kind = np.zeros(maxp, np.int32)
+    pos = np.zeros(4 * maxp, np.int32)
+    coef = np.zeros(maxp, np.int32)
+    ppass = np.zeros(maxp, np.int32)
+    tb = np.zeros(maxp, np.int32)
+    tbits = np.zeros(16 * maxp, np.int32)
+    coefs = np.zeros(2 * maxc, np.float32)
+    ncoefs = ctypes.c_int(0)
+    P = ctypes.c_void_p
+    nph = shim.tile_plan(n, kmax, int(herm), tbmax, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P),
+                         qs.ctypes.data_as(P), mats.ctypes.data_as(P), offs.ctypes.data_as(P), maxp,
+                         kind.ctypes.data_as(P), pos.ctypes.data_as(P), coef.ctypes.data_as(P),
+                         ppass.ctypes.data_as(P), maxp, tb.ctypes.data_as(P), tbits.ctypes.data_as(P), maxc,
+                         coefs.ctypes.data_as(P), ctypes.byref(ncoefs))
+    assert nph >= 0
+    cf = coefs[:2 * ncoefs.value].astype(np.float64).view(np.complex128)
+    return [(int(kind[i]), [int(x) for x in pos[4 * i:4 * i + 4]], int(coef[i]), int(tb[ppass[i]]),
+             [int(x) for x in tbits[16 * ppass[i]:16 * ppass[i] + 16]]) for i in range(nph)], cf
+
+
+def _pauli_odd(e):
+    return (((e >> 3) & 1) and not ((e >> 1) & 1)) != (((e >> 2) & 1) and not (e & 1))
+
+
+def _butterflies(x):
+    """The kernels' per-qubit butterflies on axis 0 of x (16 members, bits r_a c_a r_b c_b as
+    8, 2, 4, 1): (b00, b01, b10, b11) -> (b00 + b11, b01 + b10, b01 - b10, b00 - b11)."""
+    x = x.copy()
+    for s1, s2, offs in ((8, 2, (0, 1, 4, 5)), (4, 1, (0, 2, 8, 10))):
+        for o in offs:
+            a, b, c, d = x[o].copy(), x[o + s2].copy(), x[o + s1].copy(), x[o + s1 + s2].copy()
+            x[o], x[o + s2], x[o + s1], x[o + s1 + s2] = a + d, b + c, b - c, a - d
+    return x
+
+
+def _replay_tile_plan(rho, n, phases, cf):
+    """Apply the packed phases to rho (2^n x 2^n) the way the kernels do, in float64."""
+    flat = rho.reshape(-1).copy()
+    vbits = 2 * n
+    for kind, pos, coff, tb, tbits in phases:
+        # virtual bit of each phase position; members are flat indices differing in those bits
+        vb = [tbits[p] for p in pos[:4 if kind != 1 else 2]]
+        others = [v for v in range(vbits) if v not in vb]
+        base = np.zeros(1, dtype=np.int64)
+        for v in others:
+            base = np.concatenate([base, base | (1 << v)])
+        if kind == 1:
+            S = cf[coff:coff + 16].reshape(4, 4)
+            mem = [base | (r << vb[0]) | (c << vb[1]) for r in (0, 1) for c in (0, 1)]
+            x = np.stack([flat[m] for m in mem])
+            y = S @ x
+            for i, m in enumerate(mem):
+                flat[m] = y[i]
+            continue
+        mem = []
+        for e in range(16):
+            idx = base.copy()
+            for j in range(4):
+                if (e >> (3 - j)) & 1:
+                    idx = idx | (1 << vb[j])
+            mem.append(idx)
+        x = np.stack([flat[m] for m in mem])
+        if kind == 3:  # product: S_a on (r_a, c_a) = bits (8, 2), then S_b on (r_b, c_b) = (4, 1)
+            for S, (s1, s2, offs) in ((cf[coff:coff + 16].reshape(4, 4), (8, 2, (0, 1, 4, 5))),
+                                      (cf[coff + 16:coff + 32].reshape(4, 4), (4, 1, (0, 2, 8, 10)))):
+                for o in offs:
+                    q = np.stack([x[o], x[o + s2], x[o + s1], x[o + s1 + s2]])
+                    y = S @ q
+                    x[o], x[o + s2], x[o + s1], x[o + s1 + s2] = y
+        else:  # two-qubit phase in the Pauli basis
+            pairs = cf[coff:coff + 128]  # (R[2p][f], R[2p+1][f]) at f * 8 + p
+            R = np.zeros((16, 16))
+            for f in range(16):
+                for p in range(8):
+                    R[2 * p, f] = pairs[f * 8 + p].real
+                    R[2 * p + 1, f] = pairs[f * 8 + p].imag
+            u = _butterflies(x)
+            v = np.stack([1j * u[f] if _pauli_odd(f) else u[f] for f in range(16)])
+            c = R @ v
+            w = np.stack([-1j * c[e] if _pauli_odd(e) else c[e] for e in range(16)])
+            x = _butterflies(w)
+        for e in range(16):
+            flat[mem[e]] = x[e]
+    return flat.reshape(rho.shape)
+
+
+@pytest.mark.parametrize("n,kmax,herm,seed", [(6, 2, True, 11), (6, 4, True, 12), (5, 3, False, 13), (7, 5, True, 14)])
+def test_tile_plan_coefficients_replay_matches_oracle(shim, n, kmax, herm, seed):
+    """The packed coefficients of every phase kind, applied with the kernels' arithmetic."""
+    rng = np.random.default_rng(seed)
+    ops = _random_ops(rng, n, 50)
+    rho0 = random_rho(rng, n)
+    want = rho0.copy()
+    for kind, qs, m in ops:
+        if kind == "u":
+            oracle.apply_unitary(want, m, qs)
+        else:
+            oracle.apply_kraus(want, np.stack(m), qs)
+    phases, cf = _tile_plan(shim, n, kmax, herm, 12 if herm else 13, ops)
+    assert {p[0] for p in phases} >= {2}
+    got = _replay_tile_plan(rho0, n, phases, cf)
+    assert np.abs(got - want).max() < 2e-5  # FP32 coefficients
