@@ -118,6 +118,46 @@ static void pauli_transfer(const std::vector<c128> &S, double R[16][16])
         }
 }
 
+// One qubit: members (b00, b01, b10, b11) -> (I, X, D, Z) by the same butterflies; the real
+// 4 x 4 transfer matrix of a one-qubit superoperator S (S[e][f], e = 2 r + c) for the device's
+// v = (I, X, i D, Z), c = R v, w = (c_I, c_X, -i c_D, c_Z), x' = butterflies(w) = S x is
+// R = (1/4) d fwd(S fwd(.)) conj(d), d = i on D.
+static void pauli1_fwd(c128 *x)
+{
+    const c128 a = x[0], b = x[1], c = x[2], d = x[3];
+    x[0] = a + d, x[1] = b + c, x[2] = b - c, x[3] = a - d;
+}
+
+static void pauli_transfer1(const c128 *S, double R[4][4])
+{
+    for (int f = 0; f < 4; f++) {
+        c128 col[4] = {};
+        col[f] = 1.0;
+        pauli1_fwd(col);
+        c128 sc[4];
+        for (int e = 0; e < 4; e++) {
+            c128 acc = 0;
+            for (int g = 0; g < 4; g++) acc += S[4 * e + g] * col[g];
+            sc[e] = acc;
+        }
+        pauli1_fwd(sc);
+        for (int e = 0; e < 4; e++) {
+            c128 z = sc[e] / 4.0;
+            if (e == 2) z *= c128(0, 1);
+            if (f == 2) z *= c128(0, -1);
+            R[e][f] = z.real();
+        }
+    }
+}
+
+static void push_transfer1(const c128 *S, std::vector<float2> &out)
+{
+    double R[4][4];
+    pauli_transfer1(S, R);
+    for (int e = 0; e < 4; e++)
+        for (int f = 0; f < 4; f++) out.push_back(make_float2((float)R[e][f], (float)R[e][f]));
+}
+
 // Hermitian passes: enumeration order of the tile bits outside a phase (positions pos[0..np)).
 // The first bits are the ones whose shared-memory bank pairs (bits 0..3 of herm_phys) are
 // linearly independent, so that the 32 groups a warp handles at once spread over all 16
@@ -176,8 +216,11 @@ void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TileP
                 for (int in = 0; in < 16; in++)
                     for (int pr = 0; pr < 8; pr++)
                         out.coefs.push_back(make_float2((float)R[2 * pr][in], (float)R[2 * pr + 1][in]));
+            } else if (f.nq == PH_PRODUCT) {
+                push_transfer1(ph.S.data(), out.coefs);
+                push_transfer1(ph.S.data() + 16, out.coefs);
             } else {
-                for (const c128 &z : ph.S) out.coefs.push_back(make_float2((float)z.real(), (float)z.imag()));
+                push_transfer1(ph.S.data(), out.coefs);
             }
             out.phases.push_back(f);
         }

@@ -212,7 +212,31 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
     }
 }
 
-// One-qubit phase: 4x4 superoperator on every (row pair x column pair) group.
+// One qubit in the Pauli basis, on the quartet of x at (O, O + S2, O + S1, O + S1 + S2) after
+// the butterflies (I, X, D, Z): v = (I, X, i D, Z), c = R v with R the qubit's real 4 x 4
+// transfer matrix (coefficients as duplicated pairs (R[e][f], R[e][f]), row-major), back to
+// (c_I, c_X, -i c_D, c_Z) for the inverse butterflies.
+template <int S1, int S2, int O>
+__device__ __forceinline__ void pauli_apply4(unsigned long long (&x)[16], const unsigned long long (&r)[16])
+{
+    const float2 d = unpack2(x[O + S1]);
+    const unsigned long long v[4] = {x[O], x[O + S2], pack2(-d.y, d.x), x[O + S1 + S2]};
+    unsigned long long c[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        c[e] = 0ull;
+#pragma unroll
+        for (int f = 0; f < 4; f++) c[e] = ffma2(r[4 * e + f], v[f], c[e]);
+    }
+    const float2 cd = unpack2(c[2]);
+    x[O] = c[0];
+    x[O + S2] = c[1];
+    x[O + S1] = pack2(cd.y, -cd.x);
+    x[O + S1 + S2] = c[3];
+}
+
+// One-qubit phase on every (row pair x column pair) group, in the Pauli basis of the qubit:
+// butterflies, the real 4 x 4 transfer matrix, butterflies back.
 template <int NT = kTileThreads, bool SWZ = false>
 __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
@@ -220,49 +244,27 @@ __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, c
     const int pr = F.pos[0], pc = F.pos[1];
     const int p[2] = {pr < pc ? pr : pc, pr < pc ? pc : pr};
     const unsigned dr = member_delta<SWZ>(pr), dc = member_delta<SWZ>(pc);
-    float2 s[16];
+    const unsigned long long *S64 = reinterpret_cast<const unsigned long long *>(S);
+    unsigned long long r[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) s[i] = S[i];
+    for (int i = 0; i < 16; i++) r[i] = S64[i];
+    unsigned long long *t64 = reinterpret_cast<unsigned long long *>(tile);
     const unsigned ng = 1u << (TB - 2);
     for (unsigned g = threadIdx.x; g < ng; g += NT) {
         const unsigned b = group_base<SWZ>(g, F, p, TB - 2);
-        float2 x[4] = {tile[b], tile[b ^ dc], tile[b ^ dr], tile[b ^ dr ^ dc]};
-        float2 y[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            y[e] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int f = 0; f < 4; f++) cfma(y[e], s[4 * e + f], x[f]);
-        }
-        tile[b] = y[0];
-        tile[b ^ dc] = y[1];
-        tile[b ^ dr] = y[2];
-        tile[b ^ dr ^ dc] = y[3];
+        unsigned long long x[16];  // members 00, 01, 10, 11 in slots 0, 1, 2, 3 (S1 = 2, S2 = 1)
+        x[0] = t64[b], x[1] = t64[b ^ dc], x[2] = t64[b ^ dr], x[3] = t64[b ^ dr ^ dc];
+        pauli_quad<2, 1, 0>(x);
+        pauli_apply4<2, 1, 0>(x, r);
+        pauli_quad<2, 1, 0>(x);
+        t64[b] = x[0], t64[b ^ dc] = x[1], t64[b ^ dr] = x[2], t64[b ^ dr ^ dc] = x[3];
     }
 }
 
-// y = s x on one quartet (e = 2 r + c) of a 16-member group, members m0..m3.
-__device__ __forceinline__ void quartet4(const float2 (&s)[16], float2 (&x)[16], int m0, int m1, int m2, int m3)
-{
-    const float2 a = x[m0], b = x[m1], c = x[m2], d = x[m3];
-    float2 y[4];
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-        y[e] = make_float2(0.f, 0.f);
-        cfma(y[e], s[4 * e + 0], a);
-        cfma(y[e], s[4 * e + 1], b);
-        cfma(y[e], s[4 * e + 2], c);
-        cfma(y[e], s[4 * e + 3], d);
-    }
-    x[m0] = y[0];
-    x[m1] = y[1];
-    x[m2] = y[2];
-    x[m3] = y[3];
-}
-
-// Product phase: two one-qubit superoperators (S_a on (r_a, c_a), then S_b on (r_b, c_b);
-// they commute) on every 16-member group, in one shared-memory round trip.  Member
-// index e = 8 r_a + 4 r_b + 2 c_a + c_b.
+// Product phase: two one-qubit superoperators (S_a on (r_a, c_a) and S_b on (r_b, c_b); they
+// commute) on every 16-member group, in one shared-memory round trip and in the Pauli basis:
+// butterflies on both qubits, R_a on every quartet of qubit a, R_b on every quartet of qubit
+// b, butterflies back.  Member index e = 8 r_a + 4 r_b + 2 c_a + c_b.
 template <int NT = kTileThreads, bool SWZ = false>
 __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int TB, const FPhase &F,
                                                 const float2 *__restrict__ S)
@@ -275,31 +277,30 @@ __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int T
 #pragma unroll
         for (int b = a + 1; b < 4; b++)
             if (p[b] < p[a]) { int t = p[a]; p[a] = p[b]; p[b] = t; }
+    const unsigned long long *S64 = reinterpret_cast<const unsigned long long *>(S);
+    unsigned long long *t64 = reinterpret_cast<unsigned long long *>(tile);
+    auto member = [&](int e) {
+        return ((e & 8) ? d0 : 0u) ^ ((e & 4) ? d1 : 0u) ^ ((e & 2) ? d2 : 0u) ^ ((e & 1) ? d3 : 0u);
+    };
     const unsigned ng = 1u << (TB - 4);
     for (unsigned g = threadIdx.x; g < ng; g += NT) {
         const unsigned base = group_base<SWZ>(g, F, p, TB - 4);
-        float2 x[16];
+        unsigned long long x[16];
 #pragma unroll
-        for (int e = 0; e < 16; e++)
-            x[e] = tile[base ^ ((e & 8) ? d0 : 0u) ^ ((e & 4) ? d1 : 0u) ^ ((e & 2) ? d2 : 0u) ^ ((e & 1) ? d3 : 0u)];
-        float2 s[16];
+        for (int e = 0; e < 16; e++) x[e] = t64[base ^ member(e)];
+        pauli_butterflies(x);
+        unsigned long long r[16];
 #pragma unroll
-        for (int i = 0; i < 16; i++) s[i] = S[i];
+        for (int i = 0; i < 16; i++) r[i] = S64[i];
+        pauli_apply4<8, 2, 0>(x, r), pauli_apply4<8, 2, 1>(x, r), pauli_apply4<8, 2, 4>(x, r),
+            pauli_apply4<8, 2, 5>(x, r);
 #pragma unroll
-        for (int o = 0; o < 4; o++) {  // o = (r_b, c_b)
-            const int rb = o >> 1, cb = o & 1;
-            quartet4(s, x, 4 * rb + cb, 4 * rb + 2 + cb, 8 + 4 * rb + cb, 8 + 4 * rb + 2 + cb);
-        }
+        for (int i = 0; i < 16; i++) r[i] = S64[16 + i];
+        pauli_apply4<4, 1, 0>(x, r), pauli_apply4<4, 1, 2>(x, r), pauli_apply4<4, 1, 8>(x, r),
+            pauli_apply4<4, 1, 10>(x, r);
+        pauli_butterflies(x);
 #pragma unroll
-        for (int i = 0; i < 16; i++) s[i] = S[16 + i];
-#pragma unroll
-        for (int o = 0; o < 4; o++) {  // o = (r_a, c_a)
-            const int ra = o >> 1, ca = o & 1;
-            quartet4(s, x, 8 * ra + 2 * ca, 8 * ra + 2 * ca + 1, 8 * ra + 4 + 2 * ca, 8 * ra + 4 + 2 * ca + 1);
-        }
-#pragma unroll
-        for (int e = 0; e < 16; e++)
-            tile[base ^ ((e & 8) ? d0 : 0u) ^ ((e & 4) ? d1 : 0u) ^ ((e & 2) ? d2 : 0u) ^ ((e & 1) ? d3 : 0u)] = x[e];
+        for (int e = 0; e < 16; e++) t64[base ^ member(e)] = x[e];
     }
 }
 

@@ -51,11 +51,11 @@ __host__ __device__ inline unsigned herm_phys(unsigned e)
     return e ^ (sw << 1);
 }
 
-// Coefficients of a phase kind, in float2 units.  A two-qubit phase stores the real 16 x 16
-// transfer matrix R of its superoperator in the Pauli basis of the two qubits, for packed FP32
-// arithmetic: for input f and output pair p (outputs 2p, 2p+1) the pair (R[2p][f],
-// R[2p+1][f]), f-major (128 float2).  One- and product phases store their complex 4x4
-// superoperators row-major.
+// Coefficients of a phase kind, in float2 units, all real transfer matrices in the Pauli basis
+// of the phase's qubits, laid out for packed FP32 arithmetic.  A two-qubit phase stores its
+// 16 x 16 matrix R as pairs (R[2p][f], R[2p+1][f]) for input f and output pair p (outputs 2p,
+// 2p+1), f-major (128 float2).  A one-qubit phase stores its 4 x 4 matrix as duplicated pairs
+// (R[e][f], R[e][f]), row-major (16 float2); a product phase stores R_a then R_b that way.
 __host__ __device__ inline int phase_coefs(int nq) { return nq == PH_TWO ? 128 : nq == PH_PRODUCT ? 32 : 16; }
 
 constexpr int kTileThreads = 256;  // threads per CTA of the tile kernels

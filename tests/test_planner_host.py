@@ -4,9 +4,9 @@ The planner's passes and composed phase superoperators, replayed in order with n
 reproduce the oracle applying the original operations in order (up to complex128 rounding):
 this checks the commutation-based reordering, the phase composition and the product-phase
 split.  The packed tile plan (what the kernels receive) is replayed with the kernels'
-arithmetic -- Pauli butterflies and the real transfer matrix for two-qubit phases, complex 4 x 4
-for product and one-qubit phases -- against the oracle to FP32 accuracy: this checks the
-transfer-matrix convention and every coefficient layout without a GPU."""
+arithmetic -- Pauli butterflies and real transfer matrices (16 x 16 for two-qubit phases, 4 x 4
+per qubit for product and one-qubit phases) -- against the oracle to FP32 accuracy: this checks
+the transfer-matrix conventions and every coefficient layout without a GPU."""
 
 import ctypes
 import os
@@ -216,6 +216,19 @@ def _butterflies(x):
     return x
 
 
+def _pauli_quartet(q, R):
+    """One qubit's quartet (b00, b01, b10, b11) as the kernels treat it: butterflies to
+    (I, X, D, Z), v = (I, X, i D, Z), c = R v, back with (c_I, c_X, -i c_D, c_Z) and the same
+    butterflies."""
+    def bfly(t):
+        return np.stack([t[0] + t[3], t[1] + t[2], t[1] - t[2], t[0] - t[3]])
+    u = bfly(q)
+    u[2] = 1j * u[2]
+    c = R @ u
+    c[2] = -1j * c[2]
+    return bfly(c)
+
+
 def _replay_tile_plan(rho, n, phases, cf):
     """Apply the packed phases to rho (2^n x 2^n) the way the kernels do, in float64."""
     flat = rho.reshape(-1).copy()
@@ -228,10 +241,10 @@ def _replay_tile_plan(rho, n, phases, cf):
         for v in others:
             base = np.concatenate([base, base | (1 << v)])
         if kind == 1:
-            S = cf[coff:coff + 16].reshape(4, 4)
+            R = cf[coff:coff + 16].real.reshape(4, 4)
             mem = [base | (r << vb[0]) | (c << vb[1]) for r in (0, 1) for c in (0, 1)]
             x = np.stack([flat[m] for m in mem])
-            y = S @ x
+            y = _pauli_quartet(x, R)
             for i, m in enumerate(mem):
                 flat[m] = y[i]
             continue
@@ -243,13 +256,12 @@ def _replay_tile_plan(rho, n, phases, cf):
                     idx = idx | (1 << vb[j])
             mem.append(idx)
         x = np.stack([flat[m] for m in mem])
-        if kind == 3:  # product: S_a on (r_a, c_a) = bits (8, 2), then S_b on (r_b, c_b) = (4, 1)
-            for S, (s1, s2, offs) in ((cf[coff:coff + 16].reshape(4, 4), (8, 2, (0, 1, 4, 5))),
-                                      (cf[coff + 16:coff + 32].reshape(4, 4), (4, 1, (0, 2, 8, 10)))):
+        if kind == 3:  # product: R_a on (r_a, c_a) = bits (8, 2), R_b on (r_b, c_b) = (4, 1)
+            for R, (s1, s2, offs) in ((cf[coff:coff + 16].real.reshape(4, 4), (8, 2, (0, 1, 4, 5))),
+                                      (cf[coff + 16:coff + 32].real.reshape(4, 4), (4, 1, (0, 2, 8, 10)))):
                 for o in offs:
                     q = np.stack([x[o], x[o + s2], x[o + s1], x[o + s1 + s2]])
-                    y = S @ q
-                    x[o], x[o + s2], x[o + s1], x[o + s1 + s2] = y
+                    x[o], x[o + s2], x[o + s1], x[o + s1 + s2] = _pauli_quartet(q, R)
         else:  # two-qubit phase in the Pauli basis
             pairs = cf[coff:coff + 128]  # (R[2p][f], R[2p+1][f]) at f * 8 + p
             R = np.zeros((16, 16))
