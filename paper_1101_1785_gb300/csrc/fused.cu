@@ -35,6 +35,21 @@ __global__ void __launch_bounds__(FT, 2) k_fused_pass(float2 *__restrict__ rho, 
 }
 
 // ------------------------------------------------------------------ host runtime
+// The pass's phase headers and coefficients as a kernel parameter (read through the constant
+// cache, which keeps the coefficient broadcasts off the shared-memory pipe), for passes that
+// fit; nph < 0 marks a pass that does not (its phases then come from shared memory).
+// Every phase has a fixed slot of the largest coefficient size, so that a coefficient's address
+// is the block's base plus (uniform phase counter) x slot plus a constant.
+constexpr int kWsParamPhases = 24;
+constexpr int kWsParamSlot = 128;  // float2: phase_coefs(PH_TWO)
+struct WsParams {
+    FPhase ph[kWsParamPhases];
+    int nph;
+    int pad[3];
+    float2 coef[kWsParamPhases][kWsParamSlot];
+};
+static_assert(sizeof(WsParams) <= 32000, "kernel parameter block limit");
+
 struct CachedPlan {
     uint64_t hash = 0;
     int n = 0, k = 0, tb = 0;
@@ -43,6 +58,8 @@ struct CachedPlan {
     std::vector<int> grid;  // tiles per pass
     std::vector<size_t> smem;
     char *dbuf = nullptr;  // device copy of passes | phases | coefs
+    std::vector<WsParams> prm;  // parameter blocks of the warp-specialised kernel's passes
+    std::vector<int> prm_idx;   // per pass: index into prm, -1 if the pass has none
     size_t phase_off = 0, coef_off = 0;
     long long last_use = 0;
 };
@@ -293,7 +310,8 @@ __device__ __forceinline__ WsSmem ws_smem(unsigned char *smem)
 __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
     k_fused_herm_ws(float2 *__restrict__ rho, const FPass *__restrict__ passes, const FPhase *__restrict__ phases,
                     const float2 *__restrict__ coefs, int pass_idx, unsigned npairs,
-                    unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile)
+                    unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile,
+                    const __grid_constant__ WsParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const WsSmem sm = ws_smem(smem);
@@ -314,10 +332,13 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
             mbar_init(&sm.bars[kWsBuf + b], WC);
         }
     }
-    // phase headers and coefficients, once per CTA when they fit
+    // phase headers and coefficients: from the parameter block, else once per CTA into shared
+    // memory when they fit
+    const bool prmok = prm.nph >= 0;
     int total = 0;
-    for (int ph = 0; ph < nph; ph++) total += phase_coefs(phases[P.phase0 + ph].nq);
-    const bool pre = nph <= kWsMaxPhases && total <= kWsCoefMax;
+    if (!prmok)
+        for (int ph = 0; ph < nph; ph++) total += phase_coefs(phases[P.phase0 + ph].nq);
+    const bool pre = !prmok && nph <= kWsMaxPhases && total <= kWsCoefMax;
     if (pre) {
         int off = 0;
         for (int ph = 0; ph < nph; ph++) {
@@ -407,7 +428,9 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
         if (!ok) break;
         float2 *tile = sm.buf + (b << 12);
         for (int ph = 0; ph < nph; ph++) {
-            if (pre) {
+            if (prmok) {
+                tile_apply_phase<WC, false, true, true>(tile, 12, prm.ph[ph], prm.coef[ph]);
+            } else if (pre) {
                 tile_apply_phase<WC, false, true>(tile, 12, sm.ph[ph], sm.coef + sm.coff[ph]);
             } else {
                 const FPhase F = phases[P.phase0 + ph];
@@ -445,6 +468,23 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
     append_tile_plan(plan_passes(ops, b, e, n, k), n, tbmax, tp, herm_kernel(c));
     cp.hpass = tp.passes;
     cp.smem = tp.smem;
+    for (const FPass &fp : tp.passes) {
+        if (!fp.herm || fp.TB != 12) {
+            cp.prm_idx.push_back(-1);
+            continue;
+        }
+        cp.prm_idx.push_back((int)cp.prm.size());
+        cp.prm.emplace_back();
+        WsParams &w = cp.prm.back();
+        memset(&w, 0, sizeof w);
+        const bool fits = fp.nphase <= kWsParamPhases;
+        for (int ph = 0; fits && ph < fp.nphase; ph++) {
+            const FPhase &f = tp.phases[fp.phase0 + ph];
+            w.ph[ph] = f;
+            memcpy(&w.coef[ph][0], &tp.coefs[f.coef], sizeof(float2) * phase_coefs(f.nq));
+        }
+        w.nph = fits ? fp.nphase : -1;
+    }
     for (const FPass &fp : tp.passes) {
         if (fp.herm) {
             const unsigned long long M = 1ull << (fp.nother / 2);
@@ -606,7 +646,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             const unsigned npairs = (unsigned)hit->grid[p];
             k_fused_herm_ws<<<std::min(npairs, rt->ws_grid), WTH, ws_smem_bytes(), c->stream>>>(
                 c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), c->wait_limit ? c->wait_limit : kWsWaitLimit,
-                c->stall_tile);
+                c->stall_tile, hit->prm[hit->prm_idx[p]]);
         } else if (hit->hpass[p].herm) {
             k_fused_herm<<<hit->grid[p], HT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
         } else {

@@ -69,6 +69,22 @@ __device__ __forceinline__ void lds_coef(unsigned addr, unsigned long long &A, u
     asm volatile("ld.shared.v2.b64 {%0, %1}, [%2+%3];\n" : "=l"(A), "=l"(B) : "r"(addr), "n"(OFF));
 }
 
+// Coefficient pairs OFF / 8 and OFF / 8 + 1 of input f: from shared memory (PRM false, S a
+// shared-memory array, sf its 32-bit address plus 64 f) or by plain loads from S (PRM true: S
+// points into the kernel's parameter block, read through the constant cache).
+template <bool PRM, int OFF>
+__device__ __forceinline__ void coef_pairs(const float2 *__restrict__ S, unsigned sf, int f, unsigned long long &A,
+                                           unsigned long long &B)
+{
+    if (PRM) {
+        const unsigned long long *p = reinterpret_cast<const unsigned long long *>(S) + 8 * f + OFF / 8;
+        A = p[0];
+        B = p[1];
+    } else {
+        lds_coef<OFF>(sf, A, B);
+    }
+}
+
 // Shared-memory offset of the first member of group g of a phase (members then differ by the
 // phase deltas).  SWZ (Hermitian passes, swizzled tile): g's bits go to the phase's outside
 // bits in the order opos lists them and the result is mapped by herm_phys; otherwise they go
@@ -139,7 +155,7 @@ __device__ __forceinline__ void pauli_butterflies(unsigned long long (&x)[16])
 // Member offsets combine by XOR: without the swizzle they are disjoint bits, with it the map
 // is linear.
 // G groups per thread (g, g + NT, ...) share every coefficient load.
-template <int G, int NT = kTileThreads, bool SWZ = false>
+template <int G, int NT = kTileThreads, bool SWZ = false, bool PRM = false>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
                                             const float2 *__restrict__ S)
 {
@@ -185,7 +201,7 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
 #define QCW_PAULI_PAIRS(Q)                                 \
     {                                                      \
         unsigned long long A, B;                           \
-        lds_coef<8 * (Q)>(sf, A, B);                       \
+        coef_pairs<PRM, 8 * (Q)>(S, sf, f, A, B);          \
         _Pragma("unroll") for (int j = 0; j < G; j++)      \
         {                                                  \
             R[j][(Q)] = ffma2(A, xr[j], R[j][(Q)]);        \
@@ -305,12 +321,13 @@ __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int T
 }
 
 // Apply one phase whose coefficients are at S (shared or global memory).
-template <int NT = kTileThreads, bool UNROLL = true, bool SWZ = false>
+// PRM: S points into the kernel parameter block (see coef_pairs).
+template <int NT = kTileThreads, bool UNROLL = true, bool SWZ = false, bool PRM = false>
 __device__ __forceinline__ void tile_apply_phase(float2 *__restrict__ tile, int TB, const FPhase &F,
                                                  const float2 *__restrict__ S)
 {
     if (F.nq == PH_TWO) {
-        tile_phase2<1, NT, SWZ>(tile, TB, F, S);
+        tile_phase2<1, NT, SWZ, PRM>(tile, TB, F, S);
     } else if (F.nq == PH_PRODUCT) {
         tile_phase_prod<NT, SWZ>(tile, TB, F, S);
     } else {
