@@ -321,13 +321,16 @@ __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int T
 }
 
 // Apply one phase whose coefficients are at S (shared or global memory).
-// PRM: S points into the kernel parameter block (see coef_pairs).
+// PRM: S points into the kernel parameter block (see coef_pairs); that caller (the
+// warp-specialised pass) has the registers for two groups per thread in two-qubit phases, which
+// halves the coefficient reads and doubles the independent work per thread.
 template <int NT = kTileThreads, bool UNROLL = true, bool SWZ = false, bool PRM = false>
 __device__ __forceinline__ void tile_apply_phase(float2 *__restrict__ tile, int TB, const FPhase &F,
                                                  const float2 *__restrict__ S)
 {
     if (F.nq == PH_TWO) {
-        tile_phase2<1, NT, SWZ, PRM>(tile, TB, F, S);
+        if (PRM) tile_phase2<2, NT, SWZ, PRM>(tile, TB, F, S);
+        else tile_phase2<1, NT, SWZ, PRM>(tile, TB, F, S);
     } else if (F.nq == PH_PRODUCT) {
         tile_phase_prod<NT, SWZ>(tile, TB, F, S);
     } else {
