@@ -88,8 +88,10 @@ QCW_API qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k);
  *     the diagonal and writes the others as their conjugate transposes (half the arithmetic).
  *     A non-Hermitian matrix loaded with qcw_set_state is not preserved.  One CTA per tile.
  *   HERM_WS (and AUTO, the default): the same Hermitian pass on persistent CTAs whose
- *     producer warp loads and stores tiles while consumer warps evolve them, so memory traffic
- *     and arithmetic overlap.  Used for registers of 6 or more qubits (HERM below that).
+ *     producer warps load and store tiles while consumer warps evolve them, so memory traffic
+ *     and arithmetic overlap; each pass reads and writes only the lower triangle r >= c of rho
+ *     (a third less memory traffic), and the library completes the matrix whenever it is read
+ *     as a whole.  Used for registers of 6 or more qubits (HERM below that).
  *   TILE: one CTA per tile, no symmetry assumed.
  * Flushes queued work first. */
 #define QCW_FUSED_KERNEL_AUTO 0
@@ -108,7 +110,10 @@ QCW_API qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which);
  * Flushes queued work first.  QCW_EINVAL if stall_tile < -1. */
 QCW_API qcw_status qcw_set_fused_wait_limit(qcw_ctx *ctx, unsigned polls, int stall_tile);
 
-/* Device pointer of rho and the context's stream (borrowed; valid until destroy). */
+/* Device pointer of rho and the context's stream (borrowed; valid until destroy).  Flushes
+ * queued work and completes the matrix first (the HERM_WS pass keeps only the lower triangle
+ * r >= c current between readouts): the buffer holds all of rho for work ordered on the
+ * returned stream until the next evolution call. */
 QCW_API qcw_status qcw_get_device_state(qcw_ctx *ctx, void **dev_rho, void **cuda_stream);
 
 /* Number of qubits of the context. */

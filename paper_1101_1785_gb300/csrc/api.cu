@@ -202,8 +202,22 @@ qcw_status plain_super(qcw_ctx *c, const std::vector<c128> &s, const int *qs, in
     return QCW_OK;
 }
 
+// Half storage: the warp-specialised pass keeps only the lower triangle current; everything
+// that reads the other triangle (plain kernels, the other fused kernels, state downloads, the
+// partial trace, direct device access) completes the matrix first.
+qcw_status ensure_full(qcw_ctx *c)
+{
+    if (!c->half) return QCW_OK;
+    launch_symmetrize(c->rho, c->n, c->nsm, c->stream);
+    CKLAUNCH(c, 1);
+    c->half = false;
+    return QCW_OK;
+}
+
 qcw_status plain_apply(qcw_ctx *c, const QOp &op)
 {
+    qcw_status fs = ensure_full(c);
+    if (fs) return fs;
     if (op.kind == 1) return plain_super(c, op.m, op.qubits, op.k);
     if (op.k == 1) return plain_gate1(c, op.m.data(), op.qubits[0], op.controls, op.ncontrols);
     if (op.k == 2) return plain_gate2(c, op.m.data(), op.qubits[0], op.qubits[1], op.controls, op.ncontrols);
@@ -320,6 +334,9 @@ extern "C" qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which)
 extern "C" qcw_status qcw_get_device_state(qcw_ctx *ctx, void **dev_rho, void **cuda_stream)
 {
     CHECK_CTX(ctx);
+    qcw_status st = fused_flush(ctx);
+    if (!st) st = ensure_full(ctx);
+    if (st) return st;
     if (dev_rho) *dev_rho = ctx->rho;
     if (cuda_stream) *cuda_stream = ctx->stream;
     return QCW_OK;
@@ -367,6 +384,7 @@ extern "C" qcw_status qcw_reset(qcw_ctx *ctx)
 {
     CHECK_CTX(ctx);
     ctx->queue.clear();
+    ctx->half = false;
     qcw_status st = clear_error_word(ctx);
     if (st) return st;
     launch_zero_state(ctx->rho, ctx->n, ctx->nsm, ctx->stream);
@@ -395,6 +413,7 @@ extern "C" qcw_status qcw_set_state(qcw_ctx *ctx, const double *rho_c128)
     qcw_status st = ensure_staging(ctx);
     if (st) return st;
     ctx->queue.clear();
+    ctx->half = false;
     st = clear_error_word(ctx);
     if (st) return st;
     size_t total = (size_t)1 << (2 * ctx->n);
@@ -414,6 +433,7 @@ extern "C" qcw_status qcw_set_state_c64(qcw_ctx *ctx, const float *rho_c64)
     CHECK_CTX(ctx);
     if (!rho_c64) return set_error(QCW_EINVAL, "null state");
     ctx->queue.clear();
+    ctx->half = false;
     qcw_status st = clear_error_word(ctx);
     if (st) return st;
     size_t bytes = sizeof(float2) << (2 * ctx->n);
@@ -426,6 +446,7 @@ extern "C" qcw_status qcw_get_state(qcw_ctx *ctx, double *out)
     CHECK_CTX(ctx);
     if (!out) return set_error(QCW_EINVAL, "null output");
     qcw_status st = fused_flush(ctx);
+    if (!st) st = ensure_full(ctx);
     if (st) return st;
     st = ensure_staging(ctx);
     if (st) return st;
@@ -580,6 +601,7 @@ extern "C" qcw_status qcw_sync(qcw_ctx *ctx)
 {
     CHECK_CTX(ctx);
     qcw_status st = fused_flush(ctx);
+    if (!st) st = ensure_full(ctx);
     if (st) return st;
     CK(cudaMemcpyAsync(ctx->h_result + kErrSlot, device_error_word(ctx), sizeof(double), cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -634,7 +656,8 @@ extern "C" qcw_status qcw_purity(qcw_ctx *ctx, double *out)
     if (!out) return set_error(QCW_EINVAL, "null output");
     qcw_status st = fused_flush(ctx);
     if (st) return st;
-    launch_purity(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
+    if (ctx->half) launch_purity_lower(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
+    else launch_purity(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
     CKLAUNCH(ctx, launches_per_reduce());
     st = fetch_results(ctx);
     if (st) return st;
@@ -671,6 +694,7 @@ extern "C" qcw_status qcw_partial_trace(qcw_ctx *ctx, const int *keep, int nkeep
         if (j && keep[j] <= keep[j - 1]) return set_error(QCW_EINVAL, "kept qubits must ascend");
     }
     qcw_status st = fused_flush(ctx);
+    if (!st) st = ensure_full(ctx);
     if (st) return st;
     PTParams p{};
     p.n = n;

@@ -64,17 +64,36 @@ struct CachedPlan {
     long long last_use = 0;
 };
 
-// Measured choice of the fusion width (fuse_k = 0): the first segments of at least
-// kTuneMinOps operations run with each candidate width in turn, timed with events; once all
-// candidates have a time per operation the fastest is kept for the context's lifetime.
+// Measured choice of the fusion width (fuse_k = 0).  Segments of at least kTuneMinOps
+// operations are timed with events at a candidate width until a choice is made, then the
+// choice holds for the context's lifetime.  Segments differ too much in content for one trial
+// per width to decide, so a segment that comes back (same operations, recognised by hash, as
+// in a circuit replayed step after step) is run at the other width: after kTunePairs such
+// pairs the width with the smaller summed time wins.  Without repeats the widths alternate
+// and, after kTuneMaxTrials trials, the smaller total time per operation wins.
 constexpr int kTuneCand[2] = {4, 5};
 constexpr size_t kTuneMinOps = 64;
+constexpr int kTunePairs = 4;
+constexpr int kTuneMaxTrials = 24;
+constexpr size_t kTuneMaxSegs = 64;
+
+struct KTuneSeg {
+    uint64_t key;       // hash of the segment's operations (width-independent)
+    float ms[2];
+    bool have[2];
+};
 
 struct KTune {
-    int stage = 0;           // candidates measured so far
     int chosen = 0;          // 0 until decided
-    double ms_per_op[2] = {0, 0};
+    int trials = 0;          // trials finished
+    double ms[2] = {0, 0};   // per candidate: summed trial time
+    double ops[2] = {0, 0};  // and summed operations
+    int paired = 0;          // segments timed at both widths
+    double pms[2] = {0, 0};  // their summed times per width
+    std::vector<KTuneSeg> segs;
     bool pending = false;    // a timed trial is in flight
+    int cand = 0;            // its candidate index
+    uint64_t key = 0;        // and segment
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     size_t nops = 0;
 };
@@ -96,11 +115,28 @@ static bool tune_poll(KTune &t)
         return true;
     }
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess && t.nops) t.ms_per_op[t.stage] = ms / (double)t.nops;
+    if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess && t.nops) {
+        t.ms[t.cand] += ms;
+        t.ops[t.cand] += (double)t.nops;
+        for (KTuneSeg &sg : t.segs)
+            if (sg.key == t.key && !sg.have[t.cand]) {
+                sg.ms[t.cand] = ms;
+                sg.have[t.cand] = true;
+                if (sg.have[0] && sg.have[1]) {
+                    t.paired++;
+                    t.pms[0] += sg.ms[0];
+                    t.pms[1] += sg.ms[1];
+                }
+                break;
+            }
+    }
     cudaGetLastError();
     t.pending = false;
-    t.stage++;
-    if (t.stage == 2) t.chosen = t.ms_per_op[0] <= t.ms_per_op[1] ? kTuneCand[0] : kTuneCand[1];
+    t.trials++;
+    if (t.paired >= kTunePairs)
+        t.chosen = t.pms[0] <= t.pms[1] ? kTuneCand[0] : kTuneCand[1];
+    else if (t.trials >= kTuneMaxTrials && t.ops[0] > 0 && t.ops[1] > 0)
+        t.chosen = t.ms[0] / t.ops[0] <= t.ms[1] / t.ops[1] ? kTuneCand[0] : kTuneCand[1];
     return false;
 }
 
@@ -249,14 +285,15 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
 
 // ------------------------------------------------------------------ warp-specialised Hermitian pass
 // Persistent CTAs of kWsConsumerWarps consumer warps and kWsProducerWarps producer warps sharing
-// kWsBuf tile buffers.  CTA c takes the pairs c, c + grid, c + 2 grid, ...  The producer loads pair tiles
-// with cp.async up to kWsBuf - 1 ahead of the consumers and writes evolved tiles (and their
-// conjugate-transposed mirrors) back while the consumers work on later ones, so the pass's
-// HBM traffic overlaps its arithmetic instead of adding to it.  Hand-over is by mbarriers:
-// full[b] (every producer lane's cp.async arrival) and empty[b] (every consumer thread's
-// arrival); the producer warps split each tile's rows k and meet at a named barrier between
-// writing a buffer back and refilling it.  Every wait is bounded: on running out, the side that gave up sets the pass's
-// error word and returns, and the other side then runs out too.
+// kWsBuf tile buffers.  CTA c takes the pairs c, c + grid, c + 2 grid, ...  The producers load
+// the canonical elements of a pair (see WsPair) with cp.async up to kWsBuf - 1 tiles ahead of
+// the consumers and write the evolved canonical elements back while the consumers work on
+// later tiles, so the pass's HBM traffic overlaps its arithmetic instead of adding to it.
+// Hand-over is by mbarriers: full[b] (every producer thread, once its copies of the tile have
+// landed and been completed) and empty[b] (every consumer thread); the producer warps split
+// each tile's rows k and meet at a named barrier between writing a buffer back and refilling
+// it.  Every wait is bounded: on running out, the side that gave up sets the pass's error word
+// and returns, and the other side then runs out too.
 //
 // Tiles are 2^12 elements (six qubits); a producer lane covers tile bits 0..5 (an element
 // pair) and the loop index k the bits 6..11, so global offsets and swizzled shared-memory
@@ -271,7 +308,7 @@ constexpr int WC = 32 * kWsConsumerWarps;  // consumer threads
 constexpr int WP = 32 * kWsProducerWarps;  // producer threads
 constexpr int WTH = WC + WP;
 constexpr int kWsMaxPhases = 24;
-constexpr int kWsCoefMax = kWsBuf >= 3 ? 1536 : 512;  // float2
+constexpr int kWsCoefMax = 512;  // float2 (shared-memory fallback when the parameter block does not fit)
 constexpr unsigned kWsWaitLimit = 1u << 21;  // polls (>= 0.5 s with the 256 ns back-off)
 
 struct WsEntry {
@@ -283,6 +320,8 @@ struct WsEntry {
 struct WsSmem {
     float2 *buf;      // kWsBuf tiles of 2^12 elements
     WsEntry *tab;     // 64 entries
+    unsigned long long *bt;  // 4 x 64: tile base = bt[0][o_c & 63] + bt[1][o_c >> 6] + bt[2][o_r & 63] + bt[3][o_r >> 6]
+    int *stab;        // 32: shift s of a pair whose highest differing outside bit is hb
     float2 *coef;     // kWsCoefMax
     FPhase *ph;       // kWsMaxPhases headers
     int *coff;        // kWsMaxPhases offsets into coef
@@ -291,8 +330,32 @@ struct WsSmem {
 
 __host__ __device__ constexpr size_t ws_smem_bytes()
 {
-    return (size_t)kWsBuf * (sizeof(float2) << 12) + 64 * sizeof(WsEntry) + kWsCoefMax * sizeof(float2) +
+    return (size_t)kWsBuf * (sizeof(float2) << 12) + 64 * sizeof(WsEntry) + 256 * sizeof(unsigned long long) +
+           32 * sizeof(int) + kWsCoefMax * sizeof(float2) +
            kWsMaxPhases * sizeof(FPhase) + kWsMaxPhases * sizeof(int) + 2 * kWsBuf * sizeof(uint64_t);
+}
+
+// Canonical copy (half storage).  Element (r, c) of rho is canonical when r >= c; a pass reads
+// and writes only canonical elements, so the other triangle goes stale (the host completes it
+// before anything else reads rho).  For the pair (T_s, T_m) = ((o_r, o_c), (o_c, o_r)),
+// o_c <= o_r: if o_r == o_c the tile is on the diagonal and (er, ec) is canonical iff er >= ec;
+// else let qo be the most significant outside qubit where o_r and o_c differ (there o_r has 1)
+// and t the number of tile qubits more significant than qo: T_s's element (er, ec) is canonical
+// iff (er >> (6 - t)) >= (ec >> (6 - t)) (the top t tile qubits decide first, ties go to T_s),
+// and otherwise its transpose in T_m is.  For t = 0 all of T_s is canonical (no mirror traffic).
+struct WsPair {
+    unsigned o_r, o_c;
+    int s;      // 6 - t (0 on the diagonal)
+    bool diag;
+};
+
+__device__ __forceinline__ WsPair ws_pair(const int *stab, unsigned p, int m)
+{
+    WsPair w;
+    pair_blocked(p, 1u << m, w.o_c, w.o_r);
+    w.diag = w.o_r == w.o_c;
+    w.s = w.diag ? 0 : stab[31 - __clz(w.o_r ^ w.o_c)];
+    return w;
 }
 
 __device__ __forceinline__ WsSmem ws_smem(unsigned char *smem)
@@ -300,7 +363,9 @@ __device__ __forceinline__ WsSmem ws_smem(unsigned char *smem)
     WsSmem w;
     w.buf = reinterpret_cast<float2 *>(smem);
     w.tab = reinterpret_cast<WsEntry *>(w.buf + kWsBuf * 4096);
-    w.coef = reinterpret_cast<float2 *>(w.tab + 64);
+    w.bt = reinterpret_cast<unsigned long long *>(w.tab + 64);
+    w.stab = reinterpret_cast<int *>(w.bt + 256);
+    w.coef = reinterpret_cast<float2 *>(w.stab + 32);
     w.ph = reinterpret_cast<FPhase *>(w.coef + kWsCoefMax);
     w.coff = reinterpret_cast<int *>(w.ph + kWsMaxPhases);
     w.bars = reinterpret_cast<uint64_t *>(w.coff + kWsMaxPhases);
@@ -325,10 +390,24 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
         sm.tab[tid].ghi = g;
         sm.tab[tid].phi = herm_phys(tid << 6);
         sm.tab[tid].pm = herm_phys(tid);
+        // outside index bit j of the column half is obits[j], of the row half obits[m + j]
+        unsigned long long b[4] = {0, 0, 0, 0};
+        for (int j = 0; j < 6; j++) {
+            if (!((tid >> j) & 1u)) continue;
+            if (j < m) b[0] += 1ull << P.obits[j], b[2] += 1ull << P.obits[m + j];
+            if (6 + j < m) b[1] += 1ull << P.obits[6 + j], b[3] += 1ull << P.obits[m + 6 + j];
+        }
+        for (int h = 0; h < 4; h++) sm.bt[64 * h + tid] = b[h];
+    } else if (tid < 96) {
+        const int hb = tid - 64;  // pair whose highest differing outside column bit is hb
+        int below = 0;
+        if (hb < m)
+            for (int j = 0; j < 6; j++) below += P.tbits[j] < P.obits[hb];
+        sm.stab[hb] = below;
     }
     if (tid == 0) {
         for (int b = 0; b < kWsBuf; b++) {
-            mbar_init(&sm.bars[b], WP);
+            mbar_init(&sm.bars[b], WP);  // full: every producer thread, by its copies or after finish
             mbar_init(&sm.bars[kWsBuf + b], WC);
         }
     }
@@ -362,35 +441,70 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
             if (((2 * lane) >> j) & 1u) glo += 1ull << P.tbits[j];
         const unsigned plo = herm_phys(2 * lane);
         const unsigned pm0 = herm_phys((2 * lane) << 6), pm1 = herm_phys((2 * lane + 1) << 6);
-        auto pair_bases = [&](unsigned i, uint64_t &self, uint64_t &mirror) {
-            unsigned o_r, o_c;
-            pair_blocked(blockIdx.x + i * gridDim.x, 1u << m, o_c, o_r);
-            self = tile_base(P, ((uint64_t)o_r << m) | o_c) + glo;
-            mirror = o_r != o_c ? tile_base(P, ((uint64_t)o_c << m) | o_r) + glo : ~0ull;
+        const unsigned lc = (2 * lane);  // this lane's column pair (lc, lc + 1) of a tile row
+        auto base_of = [&](unsigned o_r, unsigned o_c) {
+            return sm.bt[o_c & 63u] + sm.bt[64 + (o_c >> 6)] + sm.bt[128 + (o_r & 63u)] + sm.bt[192 + (o_r >> 6)];
+        };
+        // Loads, row k at a time: the canonical part of T_s row k (16-byte pairs; lc and lc + 1
+        // share the top bits) and, for split pairs, the canonical part of T_m row k into the
+        // transposed slots of T_s (8-byte copies; the first phase conjugates them as it reads).  A
+        // diagonal tile is loaded whole and completed by finish.  One cp.async group per tile;
+        // tiles are released by the copies' own arrival on full, diagonal ones by finish.
+        auto needs_finish = [&](unsigned i) {
+            return ws_pair(sm.stab, blockIdx.x + i * gridDim.x, m).diag;
         };
         auto load = [&](unsigned i) {
             float2 *bf = sm.buf + ((i % kWsBuf) << 12);
-            uint64_t sb, mb;
-            pair_bases(i, sb, mb);
+            const WsPair w = ws_pair(sm.stab, blockIdx.x + i * gridDim.x, m);
+            const uint64_t sb = base_of(w.o_r, w.o_c) + glo;
+            const bool split = !w.diag && w.s < 6;
+            const uint64_t mb = split ? base_of(w.o_c, w.o_r) + glo : 0;
+            const unsigned ltop = lc >> w.s;
 #pragma unroll 4
             for (unsigned k = pw; k < 64; k += kWsProducerWarps) {
                 const WsEntry t = sm.tab[k];
-                cp_async16(bf + (plo ^ t.phi), rho + sb + t.ghi);
+                const unsigned ktop = k >> w.s;
+                if (w.diag || ktop >= ltop) cp_async16(bf + (plo ^ t.phi), rho + sb + t.ghi);
+                if (split && ltop < ktop) {  // T_m row k = T_s column k
+                    const float2 *src = rho + mb + t.ghi;
+                    cp_async8(bf + (pm0 ^ t.pm), src);
+                    cp_async8(bf + (pm1 ^ t.pm), src + 1);
+                }
             }
-            cp_async_mbar_arrive(&sm.bars[i % kWsBuf]);
+            if (!w.diag) cp_async_mbar_arrive(&sm.bars[i % kWsBuf]);
+            cp_async_commit();
         };
-        // One instruction writes one row of the tile (and one row of the mirror): row-local
-        // writes keep HBM efficient.  The element pair (t, t + 1) of the mirror is conj of tile
-        // elements swap(t), swap(t + 1).
+        // A diagonal tile's copies have landed (all lanes' after the barrier): fill its upper
+        // triangle from its lower one, then release it to the consumers.
+        auto finish = [&](unsigned i) {
+            float2 *bf = sm.buf + ((i % kWsBuf) << 12);
+            bar_sync(2, WP);
+            for (unsigned e = tid - WC; e < 4096; e += WP) {
+                const unsigned er = e >> 6, ec = e & 63u;
+                if (er < ec) {
+                    const float2 v = bf[herm_phys((ec << 6) | er)];
+                    bf[herm_phys(e)] = make_float2(v.x, -v.y);
+                }
+            }
+            if (!(blockIdx.x == 0 && (int)i == stall_tile)) mbar_arrive(&sm.bars[i % kWsBuf]);
+        };
+        // Write-back of the canonical elements, row k at a time: T_s row k and, for split pairs,
+        // T_m row k (the conjugated column k of the evolved T_s).  Row-local writes keep HBM
+        // efficient.
         auto store = [&](unsigned i) {
             const float2 *bf = sm.buf + ((i % kWsBuf) << 12);
-            uint64_t sb, mb;
-            pair_bases(i, sb, mb);
+            const WsPair w = ws_pair(sm.stab, blockIdx.x + i * gridDim.x, m);
+            const uint64_t sb = base_of(w.o_r, w.o_c) + glo;
+            const bool split = !w.diag && w.s < 6;
+            const uint64_t mb = split ? base_of(w.o_c, w.o_r) + glo : 0;
+            const unsigned ltop = lc >> w.s;
 #pragma unroll 4
             for (unsigned k = pw; k < 64; k += kWsProducerWarps) {
                 const WsEntry t = sm.tab[k];
-                *reinterpret_cast<float4 *>(rho + sb + t.ghi) = *reinterpret_cast<const float4 *>(bf + (plo ^ t.phi));
-                if (mb != ~0ull) {
+                const unsigned ktop = k >> w.s;
+                if (w.diag || ktop >= ltop)
+                    *reinterpret_cast<float4 *>(rho + sb + t.ghi) = *reinterpret_cast<const float4 *>(bf + (plo ^ t.phi));
+                if (split && ltop < ktop) {
                     const float2 a = bf[pm0 ^ t.pm], b = bf[pm1 ^ t.pm];
                     *reinterpret_cast<float4 *>(rho + mb + t.ghi) = make_float4(a.x, -a.y, b.x, -b.y);
                 }
@@ -410,6 +524,15 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
                 bar_sync(2, WP);  // every producer's reads of the buffer precede the new copies into it
             }
             if (!(blockIdx.x == 0 && (int)i == stall_tile)) load(i);
+            else cp_async_commit();
+            if (i >= 1 && needs_finish(i - 1)) {
+                cp_async_wait_group1();  // tile i - 1's group
+                finish(i - 1);
+            }
+        }
+        if (ok && ntile >= 1 && needs_finish(ntile - 1)) {
+            cp_async_wait_all();
+            finish(ntile - 1);
         }
         for (unsigned i = ntile >= kWsBuf ? ntile - kWsBuf : 0; ok && i < ntile; i++) {
             ok = wait_empty(i);
@@ -427,17 +550,20 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
         ok = bar_and(1, WC, mbar_wait(&sm.bars[b], (i / kWsBuf) & 1u, wait_limit));
         if (!ok) break;
         float2 *tile = sm.buf + (b << 12);
+        const WsPair w = ws_pair(sm.stab, blockIdx.x + i * gridDim.x, m);
+        const int cs = w.diag ? 6 : w.s;  // members copied from T_m: conjugated by the first phase
         for (int ph = 0; ph < nph; ph++) {
             if (prmok) {
-                tile_apply_phase<WC, false, true, true>(tile, 12, prm.ph[ph], prm.coef[ph]);
+                const FPhase F = prm.ph[ph];  // header in registers: its positions are read per group
+                tile_apply_phase<WC, false, true, true>(tile, 12, F, prm.coef[ph], ph == 0 ? cs : 6);
             } else if (pre) {
-                tile_apply_phase<WC, false, true>(tile, 12, sm.ph[ph], sm.coef + sm.coff[ph]);
+                tile_apply_phase<WC, false, true>(tile, 12, sm.ph[ph], sm.coef + sm.coff[ph], ph == 0 ? cs : 6);
             } else {
                 const FPhase F = phases[P.phase0 + ph];
                 const int nc = phase_coefs(F.nq);
                 for (int j = tid; j < nc; j += WC) sm.coef[j] = coefs[F.coef + j];
                 bar_sync(1, WC);
-                tile_apply_phase<WC, false, true>(tile, 12, F, sm.coef);
+                tile_apply_phase<WC, false, true>(tile, 12, F, sm.coef, ph == 0 ? cs : 6);
             }
             bar_sync(1, WC);
         }
@@ -566,7 +692,20 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     } else if (tn.chosen) {
         k = tn.chosen;
     } else if (n >= 12 && herm0 && e - b >= kTuneMinOps && !tune_poll(tn) && !tn.chosen) {
-        k = kTuneCand[tn.stage];
+        // a known segment runs at the width it has not been timed at; a new one alternates
+        const uint64_t key = hash_ops(c->queue, b, e, n, 0, 0);
+        int cand = tn.trials & 1;
+        bool found = false;
+        for (const KTuneSeg &sg : tn.segs)
+            if (sg.key == key) {
+                found = true;
+                if (sg.have[0] != sg.have[1]) cand = sg.have[0] ? 1 : 0;
+                break;
+            }
+        if (!found && tn.segs.size() < kTuneMaxSegs) tn.segs.push_back(KTuneSeg{key, {0.f, 0.f}, {false, false}});
+        tn.cand = cand;
+        tn.key = key;
+        k = kTuneCand[cand];
         trial = true;
     } else {
         k = tn.chosen ? tn.chosen : auto_k(c->queue, b, e, n, herm0, herm0 ? 12 : 13);
@@ -642,7 +781,12 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             }
             cudaEventRecord(e0, c->stream);
         }
+        if (!ws_pass(c, hit->hpass[p])) {
+            qcw_status fs = ensure_full(c);  // the other kernels read both triangles
+            if (fs) return fs;
+        }
         if (ws_pass(c, hit->hpass[p])) {
+            c->half = true;
             const unsigned npairs = (unsigned)hit->grid[p];
             k_fused_herm_ws<<<std::min(npairs, rt->ws_grid), WTH, ws_smem_bytes(), c->stream>>>(
                 c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), c->wait_limit ? c->wait_limit : kWsWaitLimit,

@@ -484,6 +484,92 @@ void launch_purity(const float2 *rho, int n, double *partials, double *out, int 
     k_fold<<<1, 32, 0, s>>>(partials, nb, 1, out);
 }
 
+// Purity of a Hermitian rho from its lower triangle: sum_r |rho_rr|^2 + 2 sum_{r > c} |rho_rc|^2.
+// Element pairs entirely above the diagonal are not read; four pairs per thread in flight.
+__device__ __forceinline__ float lower_weighted(const float4 *__restrict__ rho4, uint64_t t, int n, uint64_t dim)
+{
+    const uint64_t g = 2 * t, r = g >> n, c = g & (dim - 1);
+    if (c > r) return 0.f;
+    const float4 a = rho4[t];
+    const float w0 = c < r ? 2.f : 1.f, w1 = c + 1 < r ? 2.f : (c + 1 == r ? 1.f : 0.f);
+    return fmaf(w1, fmaf(a.z, a.z, a.w * a.w), w0 * fmaf(a.x, a.x, a.y * a.y));
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_purity_lower(const float4 *__restrict__ rho4, int n, double *partials)
+{
+    double acc[1] = {0};
+    const uint64_t dim = 1ull << n, n4 = (dim * dim) / 2;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (; t + 3 * stride < n4; t += 4 * stride) {
+        const float s0 = lower_weighted(rho4, t, n, dim), s1 = lower_weighted(rho4, t + stride, n, dim);
+        const float s2 = lower_weighted(rho4, t + 2 * stride, n, dim), s3 = lower_weighted(rho4, t + 3 * stride, n, dim);
+        acc[0] += (double)((s0 + s1) + (s2 + s3));
+    }
+    for (; t < n4; t += stride) acc[0] += (double)lower_weighted(rho4, t, n, dim);
+    block_store<1>(acc, 1, partials);
+}
+
+void launch_purity_lower(const float2 *rho, int n, double *partials, double *out, int nblocks, cudaStream_t s)
+{
+    uint64_t n4 = (1ull << (2 * n)) / 2;
+    uint64_t need = (n4 + RED_THREADS - 1) / RED_THREADS;
+    int nb = (int)(need < (uint64_t)nblocks ? need : (uint64_t)nblocks);
+    k_purity_lower<<<nb, RED_THREADS, 0, s>>>(reinterpret_cast<const float4 *>(rho), n, partials);
+    k_fold<<<1, 32, 0, s>>>(partials, nb, 1, out);
+}
+
+// Complete rho from its lower triangle: rho[r][c] = conj(rho[c][r]) for r < c.  32 x 32 blocks:
+// block (I, J), I <= J, reads the lower block (J, I) into shared memory and writes its
+// conjugate transpose (only r < c inside diagonal blocks).  Loads and stores run along rows.
+__global__ void __launch_bounds__(256) k_symmetrize(float2 *__restrict__ rho, int n)
+{
+    __shared__ float2 sh[32][33];
+    const uint64_t dim = 1ull << n;
+    const unsigned nb = (unsigned)(dim >> 5);
+    const uint64_t nblk = (uint64_t)nb * (nb + 1) / 2;
+    for (uint64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        // blk -> (I, J), I <= J, blk = J (J + 1) / 2 + I
+        uint64_t J = (uint64_t)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+        while ((J + 1) * (J + 2) / 2 <= blk) J++;
+        while (J * (J + 1) / 2 > blk) J--;
+        const uint64_t I = blk - J * (J + 1) / 2;
+        for (unsigned y = threadIdx.y; y < 32; y += 8) sh[y][threadIdx.x] = rho[(J * 32 + y) * dim + I * 32 + threadIdx.x];
+        __syncthreads();
+        for (unsigned y = threadIdx.y; y < 32; y += 8) {
+            const uint64_t r = I * 32 + y, c = J * 32 + threadIdx.x;
+            if (r < c) {
+                const float2 v = sh[threadIdx.x][y];
+                rho[r * dim + c] = make_float2(v.x, -v.y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_symmetrize_small(float2 *__restrict__ rho, int n)
+{
+    const unsigned dim = 1u << n;
+    for (unsigned e = threadIdx.x; e < dim * dim; e += blockDim.x) {
+        const unsigned r = e >> n, c = e & (dim - 1);
+        if (r < c) {
+            const float2 v = rho[(size_t)c * dim + r];
+            rho[e] = make_float2(v.x, -v.y);
+        }
+    }
+}
+
+void launch_symmetrize(float2 *rho, int n, int nsm, cudaStream_t s)
+{
+    if (n < 5) {
+        k_symmetrize_small<<<1, 256, 0, s>>>(rho, n);
+        return;
+    }
+    const uint64_t nb = 1ull << (n - 5), nblk = nb * (nb + 1) / 2;
+    const uint64_t cap = (uint64_t)nsm * 8;
+    k_symmetrize<<<(unsigned)(nblk < cap ? nblk : cap), dim3(32, 8), 0, s>>>(rho, n);
+}
+
 // Projector and renormalisation: keep (r, c) with qubit bit == m on both sides, times scale;
 // every other element becomes 0 (read only when kept).
 __global__ void k_project(float4 *__restrict__ rho4, uint64_t npairs, int pc, int pr, int m, float scale)

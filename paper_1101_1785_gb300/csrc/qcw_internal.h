@@ -73,6 +73,10 @@ void launch_diag_reduce(const float2 *rho, int n, double *partials, double *out,
 void launch_purity(const float2 *rho, int n, double *partials, double *out, int nblocks,
                    cudaStream_t s);
 void launch_project(float2 *rho, int n, int qubit, int m, float scale, int nsm, cudaStream_t s);
+// Half storage: rho[r][c] = conj(rho[c][r]) for r < c (complete the matrix from its lower
+// triangle), and purity from the lower triangle (2 |rho_rc|^2 below the diagonal).
+void launch_symmetrize(float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_purity_lower(const float2 *rho, int n, double *partials, double *out, int nblocks, cudaStream_t s);
 void launch_partial_trace(const float2 *rho, const PTParams &p, double2 *out, int nsm,
                           cudaStream_t s);
 int launches_per_reduce();
@@ -118,6 +122,9 @@ struct qcw_ctx {
     // tile whose load the first CTA skips (fault injection; -1: none)
     unsigned wait_limit = 0;
     int stall_tile = -1;
+    // half storage: only the lower triangle (r >= c) of rho is current (the warp-specialised
+    // pass leaves it so); ensure_full completes the matrix before anything else reads it
+    bool half = false;
     // counters
     long long launches = 0;
     long long passes = 0;
@@ -139,6 +146,7 @@ qcw_status fused_flush(qcw_ctx *ctx);
 void fused_destroy(qcw_ctx *ctx);
 void fused_collect_timing(qcw_ctx *ctx);
 qcw_status plain_apply(qcw_ctx *c, const QOp &op);
+qcw_status ensure_full(qcw_ctx *c);
 // Validate an op list against an n-qubit register and convert it to queued operations
 // (Kraus sets become superoperators); nothing is appended on error.
 qcw_status convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out);

@@ -19,6 +19,12 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -105,6 +111,53 @@ __device__ __forceinline__ unsigned group_base(unsigned g, const FPhase &F, cons
     return b;
 }
 
+// Logical (unswizzled) tile index of the first member of group g of a Hermitian-pass phase.
+__device__ __forceinline__ unsigned group_logical(unsigned g, const FPhase &F, int nout)
+{
+    unsigned b = 0;
+#pragma unroll
+    for (int i = 0; i < 12; i++)
+        if (i < nout) b |= ((g >> i) & 1u) << F.opos[i];
+    return b;
+}
+
+// Half storage (Hermitian passes): members whose tile element (er, ec) has
+// (er >> s) < (ec >> s) were copied from the mirror tile and must be conjugated when the
+// pass's first phase reads them; s = 6 turns this off.  Flips the sign of the imaginary half.
+__device__ __forceinline__ unsigned long long conj_if(unsigned long long x, unsigned logical, int s)
+{
+    const bool c = (logical >> (6 + s)) < ((logical & 63u) >> s);
+    return c ? x ^ 0x8000000000000000ull : x;
+}
+
+// The same test for the 16 members of a two-qubit group: R = er >> s and C = ec >> s of a
+// member are the group base's plus the contributions of the member's phase bits that fall in
+// the top region (positions pos[0], pos[1] are row bits, pos[2], pos[3] column bits).
+struct ConjTop {
+    unsigned ra, rb, ca, cb;  // top-region contribution of each phase position
+};
+
+__device__ __forceinline__ ConjTop conj_top(const FPhase &F, int s)
+{
+    auto top = [&](int pos, bool row) -> unsigned {
+        const int sh = row ? 6 + s : s;
+        if (row ? pos < 6 : pos >= 6) return 0u;
+        return pos >= sh ? 1u << (pos - sh) : 0u;
+    };
+    return ConjTop{top(F.pos[0], true), top(F.pos[1], true), top(F.pos[2], false), top(F.pos[3], false)};
+}
+
+__device__ __forceinline__ void conj_group16(unsigned long long (&x)[16], unsigned logical_base, int s, const ConjTop &T)
+{
+    const unsigned R0 = logical_base >> (6 + s), C0 = (logical_base & 63u) >> s;
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const unsigned R = R0 | ((e & 8) ? T.ra : 0u) | ((e & 4) ? T.rb : 0u);
+        const unsigned C = C0 | ((e & 2) ? T.ca : 0u) | ((e & 1) ? T.cb : 0u);
+        if (R < C) x[e] ^= 0x8000000000000000ull;
+    }
+}
+
 template <bool SWZ>
 __device__ __forceinline__ unsigned member_delta(int pos)
 {
@@ -157,7 +210,7 @@ __device__ __forceinline__ void pauli_butterflies(unsigned long long (&x)[16])
 // G groups per thread (g, g + NT, ...) share every coefficient load.
 template <int G, int NT = kTileThreads, bool SWZ = false, bool PRM = false>
 __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, const FPhase &F,
-                                            const float2 *__restrict__ S)
+                                            const float2 *__restrict__ S, int conj_s = 6)
 {
     const unsigned d0 = member_delta<SWZ>(F.pos[0]), d1 = member_delta<SWZ>(F.pos[1]),
                    d2 = member_delta<SWZ>(F.pos[2]), d3 = member_delta<SWZ>(F.pos[3]);
@@ -178,9 +231,16 @@ __device__ __forceinline__ void tile_phase2(float2 *__restrict__ tile, int TB, c
         unsigned long long x[G][16];
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            base[j] = group_base<SWZ>(g0 + j * NT, F, p, TB - 4);
+            unsigned bl = 0;
+            if (SWZ) {
+                bl = group_logical(g0 + j * NT, F, TB - 4);
+                base[j] = herm_phys(bl);
+            } else {
+                base[j] = group_base<SWZ>(g0 + j * NT, F, p, TB - 4);
+            }
 #pragma unroll
             for (int e = 0; e < 16; e++) x[j][e] = t64[base[j] ^ member(e)];
+            if (SWZ && conj_s < 6) conj_group16(x[j], bl, conj_s, conj_top(F, conj_s));
             pauli_butterflies(x[j]);
         }
         unsigned long long R[G][8], I[G][8];
@@ -255,7 +315,7 @@ __device__ __forceinline__ void pauli_apply4(unsigned long long (&x)[16], const 
 // butterflies, the real 4 x 4 transfer matrix, butterflies back.
 template <int NT = kTileThreads, bool SWZ = false>
 __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, const FPhase &F,
-                                            const float2 *__restrict__ S)
+                                            const float2 *__restrict__ S, int conj_s = 6)
 {
     const int pr = F.pos[0], pc = F.pos[1];
     const int p[2] = {pr < pc ? pr : pc, pr < pc ? pc : pr};
@@ -270,6 +330,11 @@ __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, c
         const unsigned b = group_base<SWZ>(g, F, p, TB - 2);
         unsigned long long x[16];  // members 00, 01, 10, 11 in slots 0, 1, 2, 3 (S1 = 2, S2 = 1)
         x[0] = t64[b], x[1] = t64[b ^ dc], x[2] = t64[b ^ dr], x[3] = t64[b ^ dr ^ dc];
+        if (SWZ && conj_s < 6) {
+            const unsigned bl = group_logical(g, F, TB - 2), lr = 1u << pr, lc = 1u << pc;
+            x[0] = conj_if(x[0], bl, conj_s), x[1] = conj_if(x[1], bl | lc, conj_s);
+            x[2] = conj_if(x[2], bl | lr, conj_s), x[3] = conj_if(x[3], bl | lr | lc, conj_s);
+        }
         pauli_quad<2, 1, 0>(x);
         pauli_apply4<2, 1, 0>(x, r);
         pauli_quad<2, 1, 0>(x);
@@ -283,7 +348,7 @@ __device__ __forceinline__ void tile_phase1(float2 *__restrict__ tile, int TB, c
 // b, butterflies back.  Member index e = 8 r_a + 4 r_b + 2 c_a + c_b.
 template <int NT = kTileThreads, bool SWZ = false>
 __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int TB, const FPhase &F,
-                                                const float2 *__restrict__ S)
+                                                const float2 *__restrict__ S, int conj_s = 6)
 {
     const unsigned d0 = member_delta<SWZ>(F.pos[0]), d1 = member_delta<SWZ>(F.pos[1]),
                    d2 = member_delta<SWZ>(F.pos[2]), d3 = member_delta<SWZ>(F.pos[3]);
@@ -304,6 +369,7 @@ __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int T
         unsigned long long x[16];
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = t64[base ^ member(e)];
+        if (SWZ && conj_s < 6) conj_group16(x, group_logical(g, F, TB - 4), conj_s, conj_top(F, conj_s));
         pauli_butterflies(x);
         unsigned long long r[16];
 #pragma unroll
@@ -324,17 +390,18 @@ __device__ __forceinline__ void tile_phase_prod(float2 *__restrict__ tile, int T
 // PRM: S points into the kernel parameter block (see coef_pairs); that caller (the
 // warp-specialised pass) has the registers for two groups per thread in two-qubit phases, which
 // halves the coefficient reads and doubles the independent work per thread.
+// conj_s < 6: half-storage conjugation of the members read (see conj_if), on a pass's first phase.
 template <int NT = kTileThreads, bool UNROLL = true, bool SWZ = false, bool PRM = false>
 __device__ __forceinline__ void tile_apply_phase(float2 *__restrict__ tile, int TB, const FPhase &F,
-                                                 const float2 *__restrict__ S)
+                                                 const float2 *__restrict__ S, int conj_s = 6)
 {
     if (F.nq == PH_TWO) {
-        if (PRM) tile_phase2<2, NT, SWZ, PRM>(tile, TB, F, S);
-        else tile_phase2<1, NT, SWZ, PRM>(tile, TB, F, S);
+        if (PRM) tile_phase2<2, NT, SWZ, PRM>(tile, TB, F, S, conj_s);
+        else tile_phase2<1, NT, SWZ, PRM>(tile, TB, F, S, conj_s);
     } else if (F.nq == PH_PRODUCT) {
-        tile_phase_prod<NT, SWZ>(tile, TB, F, S);
+        tile_phase_prod<NT, SWZ>(tile, TB, F, S, conj_s);
     } else {
-        tile_phase1<NT, SWZ>(tile, TB, F, S);
+        tile_phase1<NT, SWZ>(tile, TB, F, S, conj_s);
     }
 }
 

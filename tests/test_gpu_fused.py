@@ -262,3 +262,40 @@ def test_warp_specialised_wait_runs_out_and_context_recovers(q):
     d.sync()
     assert np.abs(d.get_state() - oracle.run_circuit(c)).max() <= ATOL
     d.close()
+
+
+@pytest.mark.parametrize("n", [6, 9, 11])
+def test_half_storage_readouts(q, n):
+    """The warp-specialised pass leaves only the lower triangle current.  Readouts taken in that
+    state (trace and probabilities from the diagonal, purity from the lower triangle, the
+    measurement's projection, the partial trace after the library completes the matrix) and the
+    completed state all match the oracle; a later pass on another kernel sees the full matrix."""
+    c = wl.random_circuit(n, 60, 9100 + n, "mixed", "adpd")
+    want = oracle.run_circuit(c)
+    d = q.Density(n)
+    d.set_mode(q.QCW_MODE_FUSED, 4)
+    d.set_fused_kernel(3)
+    for op in c.ops:
+        d.apply_op(op)
+    assert abs(d.trace() - oracle.trace(want)) <= TRACE_TOL
+    assert abs(d.purity() - oracle.purity(want)) <= 1e-6
+    np.testing.assert_allclose(d.probabilities(), oracle.probabilities(want), atol=1e-6, rtol=0)
+    m_ref, p_ref = oracle.measure(want, 1, 0)
+    m, p = d.measure(1, 0)
+    assert m == m_ref and abs(p - p_ref) <= 1e-6
+    assert abs(d.purity() - oracle.purity(want)) <= 1e-5
+    keep = [0, n - 1]
+    np.testing.assert_allclose(d.partial_trace(keep), oracle.partial_trace(want, keep), atol=1e-6, rtol=0)
+    # more work on the warp-specialised kernel, then on the per-tile Hermitian kernel
+    tail = wl.random_circuit(n, 20, 9200 + n, "mixed", "adpd")
+    for op in tail.ops:
+        d.apply_op(op)
+        oracle.apply_op(want, op)
+    d.set_fused_kernel(2)
+    for op in tail.ops:
+        d.apply_op(op)
+        oracle.apply_op(want, op)
+    got = d.get_state()
+    assert np.abs(got - want).max() <= ATOL
+    assert np.abs(got - got.conj().T).max() == 0.0
+    d.close()
