@@ -485,36 +485,45 @@ void launch_purity(const float2 *rho, int n, double *partials, double *out, int 
 }
 
 // Purity of a Hermitian rho from its lower triangle: sum_r |rho_rr|^2 + 2 sum_{r > c} |rho_rc|^2.
-// Element pairs entirely above the diagonal are not read; four pairs per thread in flight.
-__device__ __forceinline__ float lower_weighted(const float4 *__restrict__ rho4, uint64_t t, int n, uint64_t dim)
-{
-    const uint64_t g = 2 * t, r = g >> n, c = g & (dim - 1);
-    if (c > r) return 0.f;
-    const float4 a = rho4[t];
-    const float w0 = c < r ? 2.f : 1.f, w1 = c + 1 < r ? 2.f : (c + 1 == r ? 1.f : 0.f);
-    return fmaf(w1, fmaf(a.z, a.z, a.w * a.w), w0 * fmaf(a.x, a.x, a.y * a.y));
-}
-
+// Blocks take rows in turn; the threads of a block read the row's element pairs (2p, 2p + 1)
+// with 2p <= r contiguously, four in flight, weighting the diagonal pair at the end.
 __global__ void __launch_bounds__(RED_THREADS) k_purity_lower(const float4 *__restrict__ rho4, int n, double *partials)
 {
     double acc[1] = {0};
-    const uint64_t dim = 1ull << n, n4 = (dim * dim) / 2;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    for (; t + 3 * stride < n4; t += 4 * stride) {
-        const float s0 = lower_weighted(rho4, t, n, dim), s1 = lower_weighted(rho4, t + stride, n, dim);
-        const float s2 = lower_weighted(rho4, t + 2 * stride, n, dim), s3 = lower_weighted(rho4, t + 3 * stride, n, dim);
-        acc[0] += (double)((s0 + s1) + (s2 + s3));
+    const uint64_t dim = 1ull << n, half = dim >> 1;
+    for (uint64_t r = blockIdx.x; r < dim; r += gridDim.x) {
+        const float4 *row = rho4 + r * half;
+        const uint64_t np = r / 2 + 1;  // pairs with 2p <= r
+        const uint64_t full = r / 2;    // pairs 0 .. full - 1 lie strictly below the diagonal
+        float s = 0.f;
+        uint64_t p = threadIdx.x;
+        for (; p + 3 * RED_THREADS < full; p += 4 * RED_THREADS) {
+            const float4 a = row[p], b = row[p + RED_THREADS], c = row[p + 2 * RED_THREADS], d = row[p + 3 * RED_THREADS];
+            s = fmaf(a.x, a.x, s); s = fmaf(a.y, a.y, s); s = fmaf(a.z, a.z, s); s = fmaf(a.w, a.w, s);
+            s = fmaf(b.x, b.x, s); s = fmaf(b.y, b.y, s); s = fmaf(b.z, b.z, s); s = fmaf(b.w, b.w, s);
+            s = fmaf(c.x, c.x, s); s = fmaf(c.y, c.y, s); s = fmaf(c.z, c.z, s); s = fmaf(c.w, c.w, s);
+            s = fmaf(d.x, d.x, s); s = fmaf(d.y, d.y, s); s = fmaf(d.z, d.z, s); s = fmaf(d.w, d.w, s);
+        }
+        for (; p < full; p += RED_THREADS) {
+            const float4 a = row[p];
+            s = fmaf(a.x, a.x, s); s = fmaf(a.y, a.y, s); s = fmaf(a.z, a.z, s); s = fmaf(a.w, a.w, s);
+        }
+        float sdiag = 0.f;
+        if (threadIdx.x == 0) {  // pair 'full' holds the diagonal element (and one below it if r is odd)
+            const float4 a = row[full];
+            const float e0 = fmaf(a.x, a.x, a.y * a.y), e1 = fmaf(a.z, a.z, a.w * a.w);
+            sdiag = (r & 1) ? fmaf(2.f, e0, e1) : e0;
+        }
+        (void)np;
+        acc[0] += 2.0 * (double)s + (double)sdiag;
     }
-    for (; t < n4; t += stride) acc[0] += (double)lower_weighted(rho4, t, n, dim);
     block_store<1>(acc, 1, partials);
 }
 
 void launch_purity_lower(const float2 *rho, int n, double *partials, double *out, int nblocks, cudaStream_t s)
 {
-    uint64_t n4 = (1ull << (2 * n)) / 2;
-    uint64_t need = (n4 + RED_THREADS - 1) / RED_THREADS;
-    int nb = (int)(need < (uint64_t)nblocks ? need : (uint64_t)nblocks);
+    const uint64_t dim = 1ull << n;
+    int nb = (int)(dim < (uint64_t)nblocks ? dim : (uint64_t)nblocks);
     k_purity_lower<<<nb, RED_THREADS, 0, s>>>(reinterpret_cast<const float4 *>(rho), n, partials);
     k_fold<<<1, 32, 0, s>>>(partials, nb, 1, out);
 }
