@@ -299,3 +299,25 @@ def test_half_storage_readouts(q, n):
     assert np.abs(got - want).max() <= ATOL
     assert np.abs(got - got.conj().T).max() == 0.0
     d.close()
+
+
+def test_pass_with_more_phases_than_the_parameter_block_holds(q):
+    """Alternating two-qubit channels on five qubits at width 5 make one pass with dozens of
+    phases: the warp-specialised kernel then stages each phase's coefficients itself."""
+    n = 8
+    rng = np.random.default_rng(4242)
+    rho = random_rho(rng, n)
+    want = rho.copy()
+    d = q.Density(n)
+    d.set_state(rho)
+    d.set_mode(q.QCW_MODE_FUSED, 5)
+    d.set_fused_kernel(3)
+    pairs = [(0, 1), (1, 2), (2, 3), (3, 4), (0, 4), (1, 3)]
+    for step in range(40):
+        a, b = pairs[step % len(pairs)]
+        ks = np.stack([np.sqrt(w) * haar_unitary(rng, 4) for w in (0.7, 0.3)])
+        d.apply_kraus(ks, [a, b])
+        oracle.apply_kraus(want, ks, [a, b])
+    assert abs(d.purity() - oracle.purity(want)) <= 1e-6
+    assert np.abs(d.get_state() - want).max() <= ATOL
+    d.close()
