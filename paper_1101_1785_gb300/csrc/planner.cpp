@@ -148,33 +148,90 @@ static unsigned qmask(const QOp &op)
 
 static int popc(unsigned x) { return __builtin_popcount(x); }
 
+// All subsets of the n qubits with exactly k members, as masks.
+static std::vector<unsigned> subsets_of_size(int n, int k)
+{
+    std::vector<unsigned> out;
+    if (k > n) return out;
+    unsigned s = (1u << k) - 1u;
+    const unsigned limit = n >= 32 ? 0u : 1u << n;
+    while (s < limit || (limit == 0 && s != 0)) {
+        out.push_back(s);
+        const unsigned c = s & (0u - s), r = s + c;  // next subset of the same size (Gosper)
+        if (r == 0) break;
+        s = (((r ^ s) >> 2) / c) | r;
+    }
+    return out;
+}
+
+// Operations of rem a pass on qubit set Q can take: an operation joins when its qubits lie in Q
+// and no skipped earlier operation shares a qubit with it (they commute past the skipped ones).
+static size_t absorbable(const std::vector<unsigned> &masks, unsigned Q)
+{
+    unsigned blocked = 0;
+    size_t taken = 0;
+    for (unsigned S : masks) {
+        if ((S & ~Q) || (S & blocked)) blocked |= S;
+        else taken++;
+    }
+    return taken;
+}
+
 std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, size_t end, int n, int kmax,
-                                  bool count_only)
+                                  bool count_only, PassSearch search)
 {
     PhaseAcc acc;
     std::vector<PassPlan> passes;
     std::vector<size_t> rem;
     for (size_t i = begin; i < end; i++) rem.push_back(i);
     const unsigned all = n >= 32 ? ~0u : ((1u << n) - 1u);
+    const std::vector<unsigned> cand = search == PassSearch::BEST ? subsets_of_size(n, kmax < n ? kmax : n)
+                                                                  : std::vector<unsigned>();
+    std::vector<unsigned> masks;
     while (!rem.empty()) {
         unsigned Q = 0, blocked = 0;
         std::vector<size_t> chosen, rest;
-        for (size_t idx = 0; idx < rem.size(); idx++) {
-            size_t i = rem[idx];
-            unsigned S = qmask(ops[i]);
-            if (blocked == all) {  // every qubit is held by a skipped op: nothing more can join
-                rest.insert(rest.end(), rem.begin() + idx, rem.end());
-                break;
+        if (!cand.empty()) {
+            masks.clear();
+            for (size_t i : rem) masks.push_back(qmask(ops[i]));
+            size_t best = 0;
+            for (unsigned C : cand) {
+                const size_t t = absorbable(masks, C);
+                if (t > best) {
+                    best = t;
+                    Q = C;
+                }
             }
-            if (S & blocked) {
-                rest.push_back(i);
-                blocked |= S;
-            } else if (popc(Q | S) <= kmax) {
-                Q |= S;
-                chosen.push_back(i);
-            } else {
-                rest.push_back(i);
-                blocked |= S;
+            for (size_t idx = 0; idx < rem.size(); idx++) {
+                const unsigned S = masks[idx];
+                if ((S & ~Q) || (S & blocked)) {
+                    rest.push_back(rem[idx]);
+                    blocked |= S;
+                } else {
+                    chosen.push_back(rem[idx]);
+                }
+            }
+            unsigned used = 0;  // the qubits the taken operations touch
+            for (size_t i : chosen) used |= qmask(ops[i]);
+            Q = used;
+        } else {
+            for (size_t idx = 0; idx < rem.size(); idx++) {
+                size_t i = rem[idx];
+                unsigned S = qmask(ops[i]);
+                if (blocked == all) {  // every qubit is held by a skipped op: nothing more can join
+                    rest.insert(rest.end(), rem.begin() + idx, rem.end());
+                    break;
+                }
+                if (S & blocked) {
+                    rest.push_back(i);
+                    blocked |= S;
+                } else if (popc(Q | S) <= kmax) {
+                    Q |= S;
+                    chosen.push_back(i);
+                } else {
+                    rest.push_back(i);
+                    blocked |= S;
+                }
             }
         }
         PassPlan pp;

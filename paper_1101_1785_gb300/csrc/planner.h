@@ -24,9 +24,15 @@ struct PassPlan {
     int nops;
 };
 
+// How a pass's qubit set is chosen.  ORDER: grow it from the remaining operations in order.
+// BEST: among all kmax-qubit sets, the one that absorbs the most remaining operations (C(n,
+// kmax) candidates per pass; about a third fewer passes on random circuits, for host time that
+// suits plans that are cached and replayed).
+enum class PassSearch { ORDER, BEST };
+
 // Plan ops[begin, end) (all with k <= 2 and no controls) for an n-qubit register.  With
 // count_only the pass / phase structure is produced without composing the superoperators.
 std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, size_t end, int n, int kmax,
-                                  bool count_only = false);
+                                  bool count_only = false, PassSearch search = PassSearch::ORDER);
 
 }  // namespace qcw

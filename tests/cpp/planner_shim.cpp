@@ -7,7 +7,7 @@
 
 using namespace qcw;
 
-extern "C" int planner_phases(int n, int kmax, int nops, const int *kind, const int *k, const int *qubits,
+extern "C" int planner_phases(int n, int kmax, int search, int nops, const int *kind, const int *k, const int *qubits,
                               const double *mats, const long long *mat_off, int max_phases, int *phase_pass,
                               int *phase_nq, int *phase_q, int *phase_product, double *phase_S, int *pass_nq)
 {
@@ -23,7 +23,8 @@ extern "C" int planner_phases(int n, int kmax, int nops, const int *kind, const 
         for (int t = 0; t < dim * dim; t++)
             o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
     }
-    std::vector<PassPlan> plan = plan_passes(ops, 0, ops.size(), n, kmax);
+    std::vector<PassPlan> plan =
+        plan_passes(ops, 0, ops.size(), n, kmax, false, search ? PassSearch::BEST : PassSearch::ORDER);
     int np = 0;
     for (size_t p = 0; p < plan.size(); p++) {
         pass_nq[p] = (int)plan[p].Q.size();
@@ -46,7 +47,7 @@ extern "C" int planner_phases(int n, int kmax, int nops, const int *kind, const 
 
 // Pass / phase structure of the count-only plan (used by the fusion-width search) against the
 // full plan of the same ops: returns the number of mismatching fields (0 when they agree).
-extern "C" int planner_count_only_mismatch(int n, int kmax, int nops, const int *kind, const int *k,
+extern "C" int planner_count_only_mismatch(int n, int kmax, int search, int nops, const int *kind, const int *k,
                                            const int *qubits, const double *mats, const long long *mat_off)
 {
     std::vector<QOp> ops(nops);
@@ -61,8 +62,9 @@ extern "C" int planner_count_only_mismatch(int n, int kmax, int nops, const int 
         for (int t = 0; t < dim * dim; t++)
             o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
     }
-    const std::vector<PassPlan> a = plan_passes(ops, 0, ops.size(), n, kmax);
-    const std::vector<PassPlan> b = plan_passes(ops, 0, ops.size(), n, kmax, true);
+    const PassSearch ps = search ? PassSearch::BEST : PassSearch::ORDER;
+    const std::vector<PassPlan> a = plan_passes(ops, 0, ops.size(), n, kmax, false, ps);
+    const std::vector<PassPlan> b = plan_passes(ops, 0, ops.size(), n, kmax, true, ps);
     int bad = a.size() != b.size();
     for (size_t p = 0; p < a.size() && p < b.size(); p++) {
         bad += a[p].Q != b[p].Q;
@@ -83,7 +85,7 @@ extern "C" int planner_count_only_mismatch(int n, int kmax, int nops, const int 
 // phases, or -1 if an output array is too small.
 #include "tile.h"
 
-extern "C" int tile_plan(int n, int kmax, int herm, int tbmax, int nops, const int *kind, const int *k,
+extern "C" int tile_plan(int n, int kmax, int search, int herm, int tbmax, int nops, const int *kind, const int *k,
                          const int *qubits, const double *mats, const long long *mat_off, int max_phases,
                          int *phase_kind, int *phase_pos, int *phase_coef, int *phase_pass, int max_passes,
                          int *pass_tb, int *pass_tbits, int max_coefs, float *coefs, int *ncoefs)
@@ -101,7 +103,8 @@ extern "C" int tile_plan(int n, int kmax, int herm, int tbmax, int nops, const i
             o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
     }
     TilePlan tp;
-    append_tile_plan(plan_passes(ops, 0, ops.size(), n, kmax), n, tbmax, tp, herm != 0);
+    append_tile_plan(plan_passes(ops, 0, ops.size(), n, kmax, false, search ? PassSearch::BEST : PassSearch::ORDER),
+                     n, tbmax, tp, herm != 0);
     if ((int)tp.phases.size() > max_phases || (int)tp.passes.size() > max_passes || (int)tp.coefs.size() > max_coefs)
         return -1;
     for (size_t p = 0; p < tp.passes.size(); p++) {

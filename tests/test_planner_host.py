@@ -82,7 +82,7 @@ def _marshal(ops):
     return kinds, ks, qs, np.concatenate(mats), np.array(offs, dtype=np.int64)
 
 
-def _plan(shim, n, kmax, ops):
+def _plan(shim, n, kmax, ops, search=0):
     kinds, ks, qs, mats, offs = _marshal(ops)
     maxp = 4 * len(ops) + 8
     pp = np.zeros(maxp, np.int32)
@@ -92,7 +92,7 @@ def _plan(shim, n, kmax, ops):
     pS = np.zeros(512 * maxp, np.float64)
     passq = np.zeros(maxp, np.int32)
     P = ctypes.c_void_p
-    r = shim.planner_phases(n, kmax, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P), qs.ctypes.data_as(P),
+    r = shim.planner_phases(n, kmax, search, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P), qs.ctypes.data_as(P),
                             mats.ctypes.data_as(P), offs.ctypes.data_as(P), maxp, pp.ctypes.data_as(P),
                             pnq.ctypes.data_as(P), pq.ctypes.data_as(P), pprod.ctypes.data_as(P),
                             pS.ctypes.data_as(P), passq.ctypes.data_as(P))
@@ -129,8 +129,9 @@ def _apply_superop(rho, n, S, qubits):
     return np.einsum(expr, S, t).reshape(rho.shape)
 
 
-@pytest.mark.parametrize("n,kmax,seed", [(3, 2, 1), (4, 3, 2), (5, 4, 3), (6, 5, 4), (6, 2, 5)])
-def test_planner_replay_matches_oracle(shim, n, kmax, seed):
+@pytest.mark.parametrize("search", [0, 1])
+@pytest.mark.parametrize("n,kmax,seed", [(3, 2, 1), (4, 3, 2), (5, 4, 3), (6, 5, 4), (6, 2, 5), (9, 4, 6)])
+def test_planner_replay_matches_oracle(shim, n, kmax, seed, search):
     rng = np.random.default_rng(seed)
     ops = _random_ops(rng, n, 60)
     rho0 = random_rho(rng, n)
@@ -140,7 +141,7 @@ def test_planner_replay_matches_oracle(shim, n, kmax, seed):
             oracle.apply_unitary(want, m, qs)
         else:
             oracle.apply_kraus(want, np.stack(m), qs)
-    phases, pass_nq = _plan(shim, n, kmax, ops)
+    phases, pass_nq = _plan(shim, n, kmax, ops, search)
     assert (pass_nq <= kmax).all() and len(pass_nq) >= 1
     got = rho0.copy()
     for _, nq, (qa, qb), product, S in phases:
@@ -165,20 +166,21 @@ def test_planner_packs_disjoint_work(shim):
     assert len(pass_nq) == 1 and len(phases) == 2
 
 
+@pytest.mark.parametrize("search", [0, 1])
 @pytest.mark.parametrize("n,kmax", [(5, 3), (8, 4), (10, 5)])
-def test_count_only_plan_has_the_same_structure(shim, n, kmax):
+def test_count_only_plan_has_the_same_structure(shim, n, kmax, search):
     """The width search plans without composing superoperators; its passes and phases must be
     the ones the full plan produces."""
     rng = np.random.default_rng(n * 31 + kmax)
     ops = _random_ops(rng, n, 120)
     kinds, ks, qs, mats, offs = _marshal(ops)
     P = ctypes.c_void_p
-    bad = shim.planner_count_only_mismatch(n, kmax, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P),
+    bad = shim.planner_count_only_mismatch(n, kmax, search, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P),
                                            qs.ctypes.data_as(P), mats.ctypes.data_as(P), offs.ctypes.data_as(P))
     assert bad == 0
 
 
-def _tile_plan(shim, n, kmax, herm, tbmax, ops):
+def _tile_plan(shim, n, kmax, herm, tbmax, ops, search=0):
     kinds, ks, qs, mats, offs = _marshal(ops)
     maxp, maxc = 4 * len(ops) + 8, 256 * (4 * len(ops) + 8)
     kind = np.zeros(maxp, np.int32)
@@ -190,7 +192,7 @@ def _tile_plan(shim, n, kmax, herm, tbmax, ops):
     coefs = np.zeros(2 * maxc, np.float32)
     ncoefs = ctypes.c_int(0)
     P = ctypes.c_void_p
-    nph = shim.tile_plan(n, kmax, int(herm), tbmax, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P),
+    nph = shim.tile_plan(n, kmax, search, int(herm), tbmax, len(ops), kinds.ctypes.data_as(P), ks.ctypes.data_as(P),
                          qs.ctypes.data_as(P), mats.ctypes.data_as(P), offs.ctypes.data_as(P), maxp,
                          kind.ctypes.data_as(P), pos.ctypes.data_as(P), coef.ctypes.data_as(P),
                          ppass.ctypes.data_as(P), maxp, tb.ctypes.data_as(P), tbits.ctypes.data_as(P), maxc,
@@ -279,8 +281,9 @@ def _replay_tile_plan(rho, n, phases, cf):
     return flat.reshape(rho.shape)
 
 
+@pytest.mark.parametrize("search", [0, 1])
 @pytest.mark.parametrize("n,kmax,herm,seed", [(6, 2, True, 11), (6, 4, True, 12), (5, 3, False, 13), (7, 5, True, 14)])
-def test_tile_plan_coefficients_replay_matches_oracle(shim, n, kmax, herm, seed):
+def test_tile_plan_coefficients_replay_matches_oracle(shim, n, kmax, herm, seed, search):
     """The packed coefficients of every phase kind, applied with the kernels' arithmetic."""
     rng = np.random.default_rng(seed)
     ops = _random_ops(rng, n, 50)
@@ -291,7 +294,20 @@ def test_tile_plan_coefficients_replay_matches_oracle(shim, n, kmax, herm, seed)
             oracle.apply_unitary(want, m, qs)
         else:
             oracle.apply_kraus(want, np.stack(m), qs)
-    phases, cf = _tile_plan(shim, n, kmax, herm, 12 if herm else 13, ops)
+    phases, cf = _tile_plan(shim, n, kmax, herm, 12 if herm else 13, ops, search)
     assert {p[0] for p in phases} >= {2}
     got = _replay_tile_plan(rho0, n, phases, cf)
     assert np.abs(got - want).max() < 2e-5  # FP32 coefficients
+
+
+
+def test_best_search_packs_no_more_passes_than_order(shim):
+    """The best-absorption pass search never needs more passes than the in-order greedy one on
+    random circuits (and usually far fewer)."""
+    rng = np.random.default_rng(77)
+    n = 10
+    ops = _random_ops(rng, n, 300)
+    _, order = _plan(shim, n, 4, ops, 0)
+    _, best = _plan(shim, n, 4, ops, 1)
+    assert len(best) <= len(order)
+    assert len(best) < 0.9 * len(order)
