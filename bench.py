@@ -51,7 +51,7 @@ def parse_args():
                          "one launch; serve: Poisson request stream through the continuous-batching server")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
-    ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "herm", "herm_ws"],
+    ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "herm", "herm_ws", "herm_tc"],
                     help="kernel for large fused passes (results are identical)")
     ap.add_argument("--fuse-k", type=int, default=FUSE_K, help="qubits per fused pass")
     ap.add_argument("--qubits", type=int, default=N_QUBITS,
@@ -161,24 +161,24 @@ def design_pass_bytes(n, kernel, tile_qubits=6):
     m = 1 << (n - tile_qubits)
     tile = 8 * 4 ** tile_qubits
     pairs = m * (m + 1) // 2
-    return tile * 2 * pairs if kernel == "k_fused_herm_ws" else tile * (pairs + m * m)
+    return tile * 2 * pairs if kernel in ("k_fused_herm_ws", "k_fused_herm_tc") else tile * (pairs + m * m)
 
 
-TIMED_KERNEL = {"auto": "k_fused_herm_ws", "herm_ws": "k_fused_herm_ws", "herm": "k_fused_herm",
-                "tile": "k_fused_pass"}
+TIMED_KERNEL = {"auto": "k_fused_herm_ws", "herm_tc": "k_fused_herm_tc", "herm_ws": "k_fused_herm_ws",
+                "herm": "k_fused_herm", "tile": "k_fused_pass"}
 
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("fused.cu", "planner.cpp", "qcw_device.cuh", "tile.cuh", "tile.cpp"):
+    for f in ("fused.cu", "planner.cpp", "qcw_device.cuh", "tile.cuh", "tile.cpp", "tc.cuh"):
         with open(os.path.join(ROOT, "paper_1101_1785_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(kernel):
     """dram bytes per fused-pass launch from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", "k_fused_herm_ws_n14_traffic.txt")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_n14_traffic.txt")
     try:
         kv = {}
         with open(path) as f:
@@ -267,7 +267,7 @@ def run_ours(args):
     packed = [q.PackedOps(p) for p in parts]
     d = q.Density(nq)
     d.set_mode(q.QCW_MODE_FUSED, args.fuse_k)
-    d.set_fused_kernel({"auto": 0, "tile": 1, "herm": 2, "herm_ws": 3}[args.fused_kernel])
+    d.set_fused_kernel({"auto": 0, "tile": 1, "herm": 2, "herm_ws": 3, "herm_tc": 4}[args.fused_kernel])
     rho_ptr, stream_ptr = d.device_state()
     ext = torch.cuda.ExternalStream(stream_ptr)
 
@@ -349,7 +349,7 @@ def run_ours(args):
                        "qubits": nq, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({8 * 4 ** nq / 2**20:.0f} MiB rho vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": recorded_traffic(),
+                         "frac": achieved / hbm, "traffic": recorded_traffic(TIMED_KERNEL[args.fused_kernel]),
                          "peak_kind": peak_kind, "kernel": TIMED_KERNEL[args.fused_kernel],
                          "bytes_per_launch": per_launch_bytes,
                          "design_bytes_per_launch": design_pass_bytes(nq, TIMED_KERNEL[args.fused_kernel]),

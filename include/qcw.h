@@ -91,13 +91,19 @@ QCW_API qcw_status qcw_set_mode(qcw_ctx *ctx, int mode, int fuse_k);
  *     producer warps load and store tiles while consumer warps evolve them, so memory traffic
  *     and arithmetic overlap; each pass reads and writes only the lower triangle r >= c of rho
  *     (a third less memory traffic), and the library completes the matrix whenever it is read
- *     as a whole.  Used for registers of 6 or more qubits (HERM below that).
+ *     as a whole.  Used for registers of 6 or more qubits (HERM below that).  Phases run on
+ *     the FP32 CUDA cores.
+ *   HERM_TC: HERM_WS with the two-qubit phases, dense real 16 x 16 contractions in the Pauli
+ *     basis, on the tensor cores (tcgen05 TF32 MMAs with the 3xTF32 split and FP32
+ *     accumulation: FP32-level accuracy).  Slower than HERM_WS on GB300 (each phase waits for
+ *     its MMAs), hence not the default.
  *   TILE: one CTA per tile, no symmetry assumed.
  * Flushes queued work first. */
 #define QCW_FUSED_KERNEL_AUTO 0
 #define QCW_FUSED_KERNEL_TILE 1
 #define QCW_FUSED_KERNEL_HERM 2
 #define QCW_FUSED_KERNEL_HERM_WS 3
+#define QCW_FUSED_KERNEL_HERM_TC 4
 QCW_API qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which);
 
 /* Bounded waits inside the HERM_WS pass kernel.  Producer and consumer warps hand tiles over

@@ -208,7 +208,8 @@ class Density:
 
     def set_fused_kernel(self, which: int):
         """0 = auto (warp-specialised Hermitian from 6 qubits), 1 = one CTA per tile (no symmetry
-        assumed), 2 = Hermitian, one CTA per tile pair, 3 = warp-specialised Hermitian."""
+        assumed), 2 = Hermitian, one CTA per tile pair, 3 = warp-specialised Hermitian (FP32 CUDA
+        cores), 4 = 3 with its two-qubit phases on the tensor cores (tcgen05, 3xTF32)."""
         check(lib().qcw_set_fused_kernel(self.h, int(which)), "qcw_set_fused_kernel")
 
     def set_fused_wait_limit(self, polls: int, stall_tile: int = -1):

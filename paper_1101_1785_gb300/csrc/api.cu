@@ -324,7 +324,7 @@ extern "C" int qcw_nqubits(const qcw_ctx *ctx) { return ctx ? ctx->n : -1; }
 extern "C" qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which)
 {
     CHECK_CTX(ctx);
-    if (which < QCW_FUSED_KERNEL_AUTO || which > QCW_FUSED_KERNEL_HERM_WS) return set_error(QCW_EINVAL, "bad kernel choice");
+    if (which < QCW_FUSED_KERNEL_AUTO || which > QCW_FUSED_KERNEL_HERM_TC) return set_error(QCW_EINVAL, "bad kernel choice");
     qcw_status st = fused_flush(ctx);
     if (st) return st;
     ctx->fused_kernel = which;

@@ -15,6 +15,7 @@
 
 #include "planner.h"
 #include "qcw_internal.h"
+#include "tc.cuh"
 #include "tile.cuh"
 
 namespace qcw {
@@ -102,6 +103,7 @@ struct FusedRuntime {
     std::vector<CachedPlan> cache;
     long long tick = 0;
     unsigned ws_grid = 0;  // CTAs of the warp-specialised kernel (resident per SM x SMs)
+    unsigned tc_grid = 0;  // the same for its tensor-core variant
     std::vector<cudaEvent_t> ev_free, ev_pending;  // pairs: start, stop
     KTune tune;
 };
@@ -319,20 +321,23 @@ struct WsEntry {
 
 struct WsSmem {
     float2 *buf;      // kWsBuf tiles of 2^12 elements
+    float *tcB;       // kTcBFloats: B operand of the tensor-core phases (k_fused_herm_tc)
     WsEntry *tab;     // 64 entries
     unsigned long long *bt;  // 4 x 64: tile base = bt[0][o_c & 63] + bt[1][o_c >> 6] + bt[2][o_r & 63] + bt[3][o_r >> 6]
     int *stab;        // 32: shift s of a pair whose highest differing outside bit is hb
     float2 *coef;     // kWsCoefMax
     FPhase *ph;       // kWsMaxPhases headers
     int *coff;        // kWsMaxPhases offsets into coef
-    uint64_t *bars;   // full[kWsBuf], empty[kWsBuf]
+    uint64_t *bars;   // full[kWsBuf], empty[kWsBuf], the tensor-core phases' two MMA barriers
+    unsigned *tslot;  // tensor-memory base address (k_fused_herm_tc)
 };
 
 __host__ __device__ constexpr size_t ws_smem_bytes()
 {
-    return (size_t)kWsBuf * (sizeof(float2) << 12) + 64 * sizeof(WsEntry) + 256 * sizeof(unsigned long long) +
-           32 * sizeof(int) + kWsCoefMax * sizeof(float2) +
-           kWsMaxPhases * sizeof(FPhase) + kWsMaxPhases * sizeof(int) + 2 * kWsBuf * sizeof(uint64_t);
+    return (size_t)kWsBuf * (sizeof(float2) << 12) + kTcBFloats * sizeof(float) + 64 * sizeof(WsEntry) +
+           256 * sizeof(unsigned long long) + 32 * sizeof(int) + kWsCoefMax * sizeof(float2) +
+           kWsMaxPhases * sizeof(FPhase) + kWsMaxPhases * sizeof(int) + (2 * kWsBuf + 2) * sizeof(uint64_t) +
+           sizeof(unsigned);
 }
 
 // Canonical copy (half storage).  Element (r, c) of rho is canonical when r >= c; a pass reads
@@ -362,21 +367,25 @@ __device__ __forceinline__ WsSmem ws_smem(unsigned char *smem)
 {
     WsSmem w;
     w.buf = reinterpret_cast<float2 *>(smem);
-    w.tab = reinterpret_cast<WsEntry *>(w.buf + kWsBuf * 4096);
+    w.tcB = reinterpret_cast<float *>(w.buf + kWsBuf * 4096);
+    w.tab = reinterpret_cast<WsEntry *>(w.tcB + kTcBFloats);
     w.bt = reinterpret_cast<unsigned long long *>(w.tab + 64);
     w.stab = reinterpret_cast<int *>(w.bt + 256);
     w.coef = reinterpret_cast<float2 *>(w.stab + 32);
     w.ph = reinterpret_cast<FPhase *>(w.coef + kWsCoefMax);
     w.coff = reinterpret_cast<int *>(w.ph + kWsMaxPhases);
     w.bars = reinterpret_cast<uint64_t *>(w.coff + kWsMaxPhases);
+    w.tslot = reinterpret_cast<unsigned *>(w.bars + 2 * kWsBuf + 2);
     return w;
 }
 
-__global__ void __launch_bounds__(WTH, kWsCtasPerSm)
-    k_fused_herm_ws(float2 *__restrict__ rho, const FPass *__restrict__ passes, const FPhase *__restrict__ phases,
-                    const float2 *__restrict__ coefs, int pass_idx, unsigned npairs,
-                    unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile,
-                    const __grid_constant__ WsParams prm)
+// TC: two-qubit phases on the tensor cores (tile_phase2_tc) when the pass's coefficients are in
+// the parameter block; consumer warp 0 holds kTcCols tensor-memory columns for the kernel's life.
+template <bool TC>
+__device__ __forceinline__ void ws_pass_body(float2 *__restrict__ rho, const FPass *__restrict__ passes,
+                                             const FPhase *__restrict__ phases, const float2 *__restrict__ coefs,
+                                             int pass_idx, unsigned npairs, unsigned long long *__restrict__ err,
+                                             unsigned wait_limit, int stall_tile, const WsParams &prm)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const WsSmem sm = ws_smem(smem);
@@ -410,6 +419,15 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
             mbar_init(&sm.bars[b], WP);  // full: every producer thread, by its copies or after finish
             mbar_init(&sm.bars[kWsBuf + b], WC);
         }
+        if (TC) {
+            mbar_init(&sm.bars[2 * kWsBuf], 1);  // one tcgen05.commit per MMA batch
+            mbar_init(&sm.bars[2 * kWsBuf + 1], 1);
+            fence_mbar_init();
+        }
+    }
+    if (TC && tid < 32) {
+        tmem_alloc(sm.tslot, kTcCols);
+        tmem_relinquish();
     }
     // phase headers and coefficients: from the parameter block, else once per CTA into shared
     // memory when they fit
@@ -431,7 +449,9 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
             off += nc;
         }
     }
+    if (TC) tc_fence_before();
     __syncthreads();
+    if (TC) tc_fence_after();
     const unsigned ntile = blockIdx.x < npairs ? (npairs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (tid >= WC) {  // ---- producer warps
@@ -544,6 +564,12 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
     }
 
     // ---- consumer warps: the pass's phases on each tile in turn
+    TcState tc{};
+    if (TC) {
+        tc.tmem = *sm.tslot;
+        tc.B = sm.tcB;
+        tc.bar = sm.bars + 2 * kWsBuf;
+    }
     bool ok = true;
     for (unsigned i = 0; i < ntile; i++) {
         const unsigned b = i % kWsBuf;
@@ -555,6 +581,12 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
         for (int ph = 0; ph < nph; ph++) {
             if (prmok) {
                 const FPhase F = prm.ph[ph];  // header in registers: its positions are read per group
+                if (TC && F.nq == PH_TWO) {
+                    const bool good = tile_phase2_tc(tile, F, prm.coef[ph], tc, ph == 0 ? cs : 6, wait_limit);
+                    ok = bar_and(1, WC, good);  // also the end-of-phase barrier
+                    if (!ok) break;
+                    continue;
+                }
                 tile_apply_phase<WC, false, true, true>(tile, 12, F, prm.coef[ph], ph == 0 ? cs : 6);
             } else if (pre) {
                 tile_apply_phase<WC, false, true>(tile, 12, sm.ph[ph], sm.coef + sm.coff[ph], ph == 0 ? cs : 6);
@@ -567,23 +599,58 @@ __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
             }
             bar_sync(1, WC);
         }
+        if (!ok) break;
         mbar_arrive(&sm.bars[kWsBuf + b]);
     }
     if (!ok && tid == 0) atomicOr(err, 2ull);
+    if (TC) {
+        if (!ok && tc.batches)  // a batch that ran out may still be in flight: give it a second wait
+            for (int j = 0; j < 2; j++) mbar_wait(&tc.bar[j], (tc.batches - 1) & 1u, wait_limit);
+        tc_fence_before();
+        bar_sync(1, WC);
+        if (tid < 32) {
+            tc_fence_after();
+            tmem_dealloc(tc.tmem, kTcCols);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(WTH, kWsCtasPerSm)
+    k_fused_herm_ws(float2 *__restrict__ rho, const FPass *__restrict__ passes, const FPhase *__restrict__ phases,
+                    const float2 *__restrict__ coefs, int pass_idx, unsigned npairs,
+                    unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile,
+                    const __grid_constant__ WsParams prm)
+{
+    ws_pass_body<false>(rho, passes, phases, coefs, pass_idx, npairs, err, wait_limit, stall_tile, prm);
+}
+
+__global__ void __launch_bounds__(WTH, kWsCtasPerSm)
+    k_fused_herm_tc(float2 *__restrict__ rho, const FPass *__restrict__ passes, const FPhase *__restrict__ phases,
+                    const float2 *__restrict__ coefs, int pass_idx, unsigned npairs,
+                    unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile,
+                    const __grid_constant__ WsParams prm)
+{
+    ws_pass_body<true>(rho, passes, phases, coefs, pass_idx, npairs, err, wait_limit, stall_tile, prm);
 }
 
 static bool herm_kernel(const qcw_ctx *c)
 {
     return c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM ||
-           c->fused_kernel == QCW_FUSED_KERNEL_HERM_WS;
+           c->fused_kernel == QCW_FUSED_KERNEL_HERM_WS || c->fused_kernel == QCW_FUSED_KERNEL_HERM_TC;
 }
+
+// The warp-specialised pass with its two-qubit phases on the tensor cores.  Not the default:
+// on GB300 it runs the 14-qubit benchmark's passes at 1.18 ms against 1.14 ms on the CUDA cores
+// (each phase's MMA round trip is a latency chain that two CTAs per SM cannot hide).
+static bool tc_kernel(const qcw_ctx *c) { return c->fused_kernel == QCW_FUSED_KERNEL_HERM_TC; }
 
 // Passes the warp-specialised kernel takes: Hermitian, 2^12-element tiles with column bit 0 of
 // rho inside (element pairs contiguous in global memory).
 static bool ws_pass(const qcw_ctx *c, const FPass &fp)
 {
-    return (c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM_WS) && fp.herm &&
-           fp.TB == 12 && fp.L >= 1;
+    return (c->fused_kernel == QCW_FUSED_KERNEL_AUTO || c->fused_kernel == QCW_FUSED_KERNEL_HERM_WS ||
+            c->fused_kernel == QCW_FUSED_KERNEL_HERM_TC) &&
+           fp.herm && fp.TB == 12 && fp.L >= 1;
 }
 
 static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, size_t e, int k, int tbmax,
@@ -750,14 +817,22 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     for (size_t p = 0; p < hit->smem.size(); p++) maxsm = std::max(maxsm, hit->smem[p]);
     qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm), maxsm);
+    const bool tc = tc_kernel(c);
+    const void *wsk = tc ? reinterpret_cast<const void *>(k_fused_herm_tc) : reinterpret_cast<const void *>(k_fused_herm_ws);
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm_ws), ws_smem_bytes());
+    if (!sst && tc) sst = ensure_smem_attr(wsk, ws_smem_bytes());
     if (sst) return sst;
-    if (!rt->ws_grid) {
+    unsigned &wgrid = tc ? rt->tc_grid : rt->ws_grid;
+    if (!wgrid) {
+        // Both kernels have the same registers, threads and shared memory; the occupancy query
+        // on the tensor-core one reports a single CTA per SM, so it takes the other's answer,
+        // capped by its kTcCols of the SM's 512 tensor-memory columns per CTA.
         int per_sm = 0;
         cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, reinterpret_cast<const void *>(k_fused_herm_ws), WTH, ws_smem_bytes());
         if (oe != cudaSuccess) return cuda_error(oe, "occupancy");
-        rt->ws_grid = (unsigned)std::max(1, per_sm) * (unsigned)c->nsm;
+        if (tc) per_sm = std::min(per_sm, 512 / kTcCols);
+        wgrid = (unsigned)std::max(1, per_sm) * (unsigned)c->nsm;
     }
     if (trial) {
         if (!tn.e0) {
@@ -788,9 +863,15 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
         if (ws_pass(c, hit->hpass[p])) {
             c->half = true;
             const unsigned npairs = (unsigned)hit->grid[p];
-            k_fused_herm_ws<<<std::min(npairs, rt->ws_grid), WTH, ws_smem_bytes(), c->stream>>>(
-                c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), c->wait_limit ? c->wait_limit : kWsWaitLimit,
-                c->stall_tile, hit->prm[hit->prm_idx[p]]);
+            const unsigned wl = c->wait_limit ? c->wait_limit : kWsWaitLimit;
+            if (tc)
+                k_fused_herm_tc<<<std::min(npairs, wgrid), WTH, ws_smem_bytes(), c->stream>>>(
+                    c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), wl, c->stall_tile,
+                    hit->prm[hit->prm_idx[p]]);
+            else
+                k_fused_herm_ws<<<std::min(npairs, wgrid), WTH, ws_smem_bytes(), c->stream>>>(
+                    c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), wl, c->stall_tile,
+                    hit->prm[hit->prm_idx[p]]);
         } else if (hit->hpass[p].herm) {
             k_fused_herm<<<hit->grid[p], HT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
         } else {

@@ -201,11 +201,11 @@ def test_persistent_pipeline_matches_plain_n12(q):
 @pytest.mark.parametrize("n", [6, 8, 11])
 def test_hermitian_kernel_matches_general_kernels(q, n):
     """The Hermitian pass kernels (tiles on or above the diagonal, mirrors written as conjugate
-    transposes; one CTA per tile pair, and the warp-specialised persistent one) against the
-    general per-tile kernel and, at n = 6 and 8, the oracle."""
+    transposes; one CTA per tile pair, the warp-specialised persistent one and its tensor-core
+    variant) against the general per-tile kernel and, at n = 6 and 8, the oracle."""
     c = wl.random_circuit(n, 80, 808 + n, "mixed", "adpd")
     got = {}
-    for which in (1, 2, 3):
+    for which in (1, 2, 3, 4):
         d = q.Density(n)
         d.set_mode(q.QCW_MODE_FUSED, 5)
         d.set_fused_kernel(which)
@@ -217,8 +217,12 @@ def test_hermitian_kernel_matches_general_kernels(q, n):
     assert np.abs(got[2] - got[2].conj().T).max() <= 1e-7
     # same tile layout and phase arithmetic: the two Hermitian kernels agree bit for bit
     np.testing.assert_array_equal(got[3], got[2])
+    # 3xTF32 tensor-core phases: FP32-level agreement, not bitwise
+    assert np.abs(got[4] - got[3]).max() <= 1e-6
     if n <= 8:
-        assert np.abs(got[3] - oracle.run_circuit(c)).max() <= ATOL
+        want = oracle.run_circuit(c)
+        assert np.abs(got[3] - want).max() <= ATOL
+        assert np.abs(got[4] - want).max() <= ATOL
 
 
 @pytest.mark.parametrize("k", [4, 5])
@@ -227,7 +231,7 @@ def test_hermitian_kernel_at_n12(q, k):
     general per-tile kernel."""
     c = wl.random_circuit(12, 60, 1200 + k, "mixed", "adpd")
     got = {}
-    for w in (1, 2, 3):
+    for w in (1, 2, 3, 4):
         d = q.Density(12)
         d.set_mode(q.QCW_MODE_FUSED, k)
         d.set_fused_kernel(w)
@@ -237,9 +241,11 @@ def test_hermitian_kernel_at_n12(q, k):
         d.close()
     assert np.abs(got[2] - got[1]).max() <= 1e-6
     np.testing.assert_array_equal(got[3], got[2])
+    assert np.abs(got[4] - got[3]).max() <= 1e-6
 
 
-def test_warp_specialised_wait_runs_out_and_context_recovers(q):
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_warp_specialised_wait_runs_out_and_context_recovers(q, kernel):
     """The first CTA skips the load of its first tile: its consumers' bounded wait runs out,
     the producer's wait for them runs out next, the kernel ends and the following readout
     reports QCW_ETIMEOUT (sticky until reset).  After a reset the context works again."""
@@ -247,7 +253,7 @@ def test_warp_specialised_wait_runs_out_and_context_recovers(q):
     c = wl.random_circuit(n, 40, 4040, "mixed", "adpd")
     d = q.Density(n)
     d.set_mode(q.QCW_MODE_FUSED, 4)
-    d.set_fused_kernel(3)
+    d.set_fused_kernel(kernel)
     d.set_fused_wait_limit(2000, 0)
     for op in c.ops:
         d.apply_op(op)
@@ -264,8 +270,9 @@ def test_warp_specialised_wait_runs_out_and_context_recovers(q):
     d.close()
 
 
+@pytest.mark.parametrize("kernel", [3, 4])
 @pytest.mark.parametrize("n", [6, 9, 11])
-def test_half_storage_readouts(q, n):
+def test_half_storage_readouts(q, n, kernel):
     """The warp-specialised pass leaves only the lower triangle current.  Readouts taken in that
     state (trace and probabilities from the diagonal, purity from the lower triangle, the
     measurement's projection, the partial trace after the library completes the matrix) and the
@@ -274,7 +281,7 @@ def test_half_storage_readouts(q, n):
     want = oracle.run_circuit(c)
     d = q.Density(n)
     d.set_mode(q.QCW_MODE_FUSED, 4)
-    d.set_fused_kernel(3)
+    d.set_fused_kernel(kernel)
     for op in c.ops:
         d.apply_op(op)
     assert abs(d.trace() - oracle.trace(want)) <= TRACE_TOL
@@ -301,7 +308,8 @@ def test_half_storage_readouts(q, n):
     d.close()
 
 
-def test_pass_with_more_phases_than_the_parameter_block_holds(q):
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_pass_with_more_phases_than_the_parameter_block_holds(q, kernel):
     """Alternating two-qubit channels on five qubits at width 5 make one pass with dozens of
     phases: the warp-specialised kernel then stages each phase's coefficients itself."""
     n = 8
@@ -311,7 +319,7 @@ def test_pass_with_more_phases_than_the_parameter_block_holds(q):
     d = q.Density(n)
     d.set_state(rho)
     d.set_mode(q.QCW_MODE_FUSED, 5)
-    d.set_fused_kernel(3)
+    d.set_fused_kernel(kernel)
     pairs = [(0, 1), (1, 2), (2, 3), (3, 4), (0, 4), (1, 3)]
     for step in range(40):
         a, b = pairs[step % len(pairs)]
