@@ -238,24 +238,63 @@ std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, siz
         pp.nops = (int)chosen.size();
         for (int q = 0; q < n; q++)
             if (Q & (1u << q)) pp.Q.push_back(q);
-        // phases of at most two qubits
-        std::vector<size_t> prem = chosen;
-        while (!prem.empty()) {
-            unsigned P = 0, pblocked = 0;
-            std::vector<size_t> pch, prest;
-            for (size_t i : prem) {
-                unsigned S = qmask(ops[i]);
-                if (S & pblocked) {
-                    prest.push_back(i);
-                    pblocked |= S;
-                } else if (popc(P | S) <= 2) {
-                    P |= S;
-                    pch.push_back(i);
-                } else {
-                    prest.push_back(i);
-                    pblocked |= S;
-                }
+        // Phases of at most two qubits, anchored on the two-qubit operations.  Walking the
+        // pass's operations in order: a two-qubit op on (a, b) joins the last phase of a if
+        // that phase is also the last of b (same pair), else opens a phase that also takes the
+        // single-qubit ops on a and b not yet placed (all earlier, commuting with everything
+        // between); a single-qubit op on q joins the last phase touching q (no later phase
+        // touches q, so it commutes past them) or waits for q's first two-qubit op.  Qubits
+        // with no two-qubit op in the pass pair up into product phases (one left over: a
+        // one-qubit phase), placed first: they share no qubit with the other phases.
+        struct Grp {
+            unsigned P;
+            std::vector<size_t> ops;
+            bool linked;
+        };
+        std::vector<Grp> grp;
+        int last[32];
+        std::vector<size_t> pend[32];
+        for (int q = 0; q < 32; q++) last[q] = -1;
+        for (size_t i : chosen) {
+            const QOp &op = ops[i];
+            if (op.k == 1) {
+                const int q = op.qubits[0];
+                if (last[q] >= 0) grp[last[q]].ops.push_back(i);
+                else pend[q].push_back(i);
+                continue;
             }
+            const int a = op.qubits[0], b = op.qubits[1];
+            if (last[a] >= 0 && last[a] == last[b]) {
+                grp[last[a]].ops.push_back(i);
+                continue;
+            }
+            Grp g{(1u << a) | (1u << b), {}, true};
+            g.ops.insert(g.ops.end(), pend[a].begin(), pend[a].end());
+            g.ops.insert(g.ops.end(), pend[b].begin(), pend[b].end());
+            g.ops.push_back(i);
+            pend[a].clear();
+            pend[b].clear();
+            last[a] = last[b] = (int)grp.size();
+            grp.push_back(std::move(g));
+        }
+        std::vector<Grp> order;
+        int lone = -1;
+        for (int q = 0; q < n; q++) {
+            if (pend[q].empty()) continue;
+            if (lone < 0) {
+                lone = q;
+                continue;
+            }
+            Grp g{(1u << lone) | (1u << q), pend[lone], false};
+            g.ops.insert(g.ops.end(), pend[q].begin(), pend[q].end());
+            order.push_back(std::move(g));
+            lone = -1;
+        }
+        if (lone >= 0) order.push_back(Grp{1u << lone, pend[lone], false});
+        for (Grp &g : grp) order.push_back(std::move(g));
+        for (const Grp &g : order) {
+            const unsigned P = g.P;
+            const std::vector<size_t> &pch = g.ops;
             PhasePlan ph;
             ph.nq = popc(P);
             ph.qa = ph.qb = -1;
@@ -265,9 +304,7 @@ std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, siz
                     else ph.qb = q;
                 }
             ph.nops = (int)pch.size();
-            bool linked = false;  // does a two-qubit op tie the phase's qubits together?
-            for (size_t i : pch) linked |= ops[i].k == 2;
-            ph.product = ph.nq == 2 && !linked;
+            ph.product = ph.nq == 2 && !g.linked;
             if (count_only) {
                 identity(ph.S, 0);
             } else if (ph.product) {
@@ -288,7 +325,6 @@ std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, siz
                 acc.result(ph.S);
             }
             pp.phases.push_back(std::move(ph));
-            prem.swap(prest);
         }
         passes.push_back(std::move(pp));
         rem.swap(rest);
