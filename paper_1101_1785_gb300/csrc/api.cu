@@ -216,6 +216,7 @@ qcw_status ensure_full(qcw_ctx *c)
 
 qcw_status plain_apply(qcw_ctx *c, const QOp &op)
 {
+    c->state_ver++;
     qcw_status fs = ensure_full(c);
     if (fs) return fs;
     if (op.kind == 1) return plain_super(c, op.m, op.qubits, op.k);
@@ -339,6 +340,7 @@ extern "C" qcw_status qcw_get_device_state(qcw_ctx *ctx, void **dev_rho, void **
     if (st) return st;
     if (dev_rho) *dev_rho = ctx->rho;
     if (cuda_stream) *cuda_stream = ctx->stream;
+    ctx->state_ver++;  // the caller may write rho
     return QCW_OK;
 }
 
@@ -385,6 +387,7 @@ extern "C" qcw_status qcw_reset(qcw_ctx *ctx)
     CHECK_CTX(ctx);
     ctx->queue.clear();
     ctx->half = false;
+    ctx->state_ver++;
     qcw_status st = clear_error_word(ctx);
     if (st) return st;
     launch_zero_state(ctx->rho, ctx->n, ctx->nsm, ctx->stream);
@@ -414,6 +417,7 @@ extern "C" qcw_status qcw_set_state(qcw_ctx *ctx, const double *rho_c128)
     if (st) return st;
     ctx->queue.clear();
     ctx->half = false;
+    ctx->state_ver++;
     st = clear_error_word(ctx);
     if (st) return st;
     size_t total = (size_t)1 << (2 * ctx->n);
@@ -434,6 +438,7 @@ extern "C" qcw_status qcw_set_state_c64(qcw_ctx *ctx, const float *rho_c64)
     if (!rho_c64) return set_error(QCW_EINVAL, "null state");
     ctx->queue.clear();
     ctx->half = false;
+    ctx->state_ver++;
     qcw_status st = clear_error_word(ctx);
     if (st) return st;
     size_t bytes = sizeof(float2) << (2 * ctx->n);
@@ -656,9 +661,16 @@ extern "C" qcw_status qcw_purity(qcw_ctx *ctx, double *out)
     if (!out) return set_error(QCW_EINVAL, "null output");
     qcw_status st = fused_flush(ctx);
     if (st) return st;
-    if (ctx->half) launch_purity_lower(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
-    else launch_purity(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
-    CKLAUNCH(ctx, launches_per_reduce());
+    const double *part = nullptr;
+    int nb = 0;
+    if (fused_purity_partials(ctx, &part, &nb)) {
+        launch_fold(part, nb, ctx->d_result, ctx->stream);  // summed by the last pass as it wrote rho
+        CKLAUNCH(ctx, 1);
+    } else {
+        if (ctx->half) launch_purity_lower(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
+        else launch_purity(ctx->rho, ctx->n, ctx->d_partials, ctx->d_result, ctx->red_blocks, ctx->stream);
+        CKLAUNCH(ctx, launches_per_reduce());
+    }
     st = fetch_results(ctx);
     if (st) return st;
     *out = ctx->h_result[0];
@@ -679,6 +691,7 @@ extern "C" qcw_status qcw_measure(qcw_ctx *ctx, int qubit, int forced, double u,
     if (outcome) *outcome = m;
     if (prob) *prob = pm;
     if (!(pm >= 1e-12)) return set_error(QCW_EZEROPROB, "outcome probability below 1e-12");
+    ctx->state_ver++;
     launch_project(ctx->rho, ctx->n, qubit, m, (float)(1.0 / pm), ctx->nsm, ctx->stream);
     CKLAUNCH(ctx, 1);
     return QCW_OK;

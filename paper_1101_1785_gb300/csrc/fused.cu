@@ -104,6 +104,9 @@ struct FusedRuntime {
     long long tick = 0;
     unsigned ws_grid = 0;  // CTAs of the warp-specialised kernel (resident per SM x SMs)
     unsigned tc_grid = 0;  // the same for its tensor-core variant
+    double *d_ppart = nullptr;  // per-CTA purity partials of the last pass of a flush
+    int ppart_nb = 0;           // CTAs that wrote them
+    int ppart_cap = 0;
     std::vector<cudaEvent_t> ev_free, ev_pending;  // pairs: start, stop
     KTune tune;
 };
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(HT, 4) k_fused_herm(float2 *__restrict__ rho, 
 // fit (else each phase's coefficients are staged before it runs).
 constexpr int kWsBuf = 3;
 constexpr int kWsConsumerWarps = 4;
-constexpr int kWsProducerWarps = 2;
+constexpr int kWsProducerWarps = 2;  // the purity epilogue sums exactly two warps' totals
 constexpr int kWsCtasPerSm = 2;
 constexpr int WC = 32 * kWsConsumerWarps;  // consumer threads
 constexpr int WP = 32 * kWsProducerWarps;  // producer threads
@@ -329,6 +332,7 @@ struct WsSmem {
     FPhase *ph;       // kWsMaxPhases headers
     int *coff;        // kWsMaxPhases offsets into coef
     uint64_t *bars;   // full[kWsBuf], empty[kWsBuf], the tensor-core phases' two MMA barriers
+    double *psum;     // 2: the producer warps' purity sums
     unsigned *tslot;  // tensor-memory base address (k_fused_herm_tc)
 };
 
@@ -337,7 +341,7 @@ __host__ __device__ constexpr size_t ws_smem_bytes()
     return (size_t)kWsBuf * (sizeof(float2) << 12) + kTcBFloats * sizeof(float) + 64 * sizeof(WsEntry) +
            256 * sizeof(unsigned long long) + 32 * sizeof(int) + kWsCoefMax * sizeof(float2) +
            kWsMaxPhases * sizeof(FPhase) + kWsMaxPhases * sizeof(int) + (2 * kWsBuf + 2) * sizeof(uint64_t) +
-           sizeof(unsigned);
+           2 * sizeof(double) + sizeof(unsigned);
 }
 
 // Canonical copy (half storage).  Element (r, c) of rho is canonical when r >= c; a pass reads
@@ -375,17 +379,20 @@ __device__ __forceinline__ WsSmem ws_smem(unsigned char *smem)
     w.ph = reinterpret_cast<FPhase *>(w.coef + kWsCoefMax);
     w.coff = reinterpret_cast<int *>(w.ph + kWsMaxPhases);
     w.bars = reinterpret_cast<uint64_t *>(w.coff + kWsMaxPhases);
-    w.tslot = reinterpret_cast<unsigned *>(w.bars + 2 * kWsBuf + 2);
+    w.psum = reinterpret_cast<double *>(w.bars + 2 * kWsBuf + 2);
+    w.tslot = reinterpret_cast<unsigned *>(w.psum + 2);
     return w;
 }
 
 // TC: two-qubit phases on the tensor cores (tile_phase2_tc) when the pass's coefficients are in
 // the parameter block; consumer warp 0 holds kTcCols tensor-memory columns for the kernel's life.
-template <bool TC>
+// PUR: also sum w |x|^2 over the write-back (purity_part, one partial per CTA).
+template <bool TC, bool PUR>
 __device__ __forceinline__ void ws_pass_body(float2 *__restrict__ rho, const FPass *__restrict__ passes,
                                              const FPhase *__restrict__ phases, const float2 *__restrict__ coefs,
                                              int pass_idx, unsigned npairs, unsigned long long *__restrict__ err,
-                                             unsigned wait_limit, int stall_tile, const WsParams &prm)
+                                             unsigned wait_limit, int stall_tile, double *__restrict__ purity_part,
+                                             const WsParams &prm)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const WsSmem sm = ws_smem(smem);
@@ -510,8 +517,12 @@ __device__ __forceinline__ void ws_pass_body(float2 *__restrict__ rho, const FPa
         };
         // Write-back of the canonical elements, row k at a time: T_s row k and, for split pairs,
         // T_m row k (the conjugated column k of the evolved T_s).  Row-local writes keep HBM
-        // efficient.
-        auto store = [&](unsigned i) {
+        // efficient.  With purity_part it also returns the sum of w |x|^2 over what it writes:
+        // w = 2 below the diagonal of rho (the mirror element is not stored), 1 on it; a
+        // diagonal tile (written whole) counts its upper triangle 0.
+        constexpr bool pur = PUR;
+        auto store = [&](unsigned i) -> float {
+            float ps = 0.f;
             const float2 *bf = sm.buf + ((i % kWsBuf) << 12);
             const WsPair w = ws_pair(sm.stab, blockIdx.x + i * gridDim.x, m);
             const uint64_t sb = base_of(w.o_r, w.o_c) + glo;
@@ -522,13 +533,23 @@ __device__ __forceinline__ void ws_pass_body(float2 *__restrict__ rho, const FPa
             for (unsigned k = pw; k < 64; k += kWsProducerWarps) {
                 const WsEntry t = sm.tab[k];
                 const unsigned ktop = k >> w.s;
-                if (w.diag || ktop >= ltop)
-                    *reinterpret_cast<float4 *>(rho + sb + t.ghi) = *reinterpret_cast<const float4 *>(bf + (plo ^ t.phi));
+                if (w.diag || ktop >= ltop) {
+                    const float4 v = *reinterpret_cast<const float4 *>(bf + (plo ^ t.phi));
+                    *reinterpret_cast<float4 *>(rho + sb + t.ghi) = v;
+                    if (pur) {
+                        const float e0 = fmaf(v.x, v.x, v.y * v.y), e1 = fmaf(v.z, v.z, v.w * v.w);
+                        const float w0 = !w.diag || k > lc ? 2.f : k == lc ? 1.f : 0.f;
+                        const float w1 = !w.diag || k > lc + 1 ? 2.f : k == lc + 1 ? 1.f : 0.f;
+                        ps = fmaf(w0, e0, fmaf(w1, e1, ps));
+                    }
+                }
                 if (split && ltop < ktop) {
                     const float2 a = bf[pm0 ^ t.pm], b = bf[pm1 ^ t.pm];
                     *reinterpret_cast<float4 *>(rho + mb + t.ghi) = make_float4(a.x, -a.y, b.x, -b.y);
+                    if (pur) ps = fmaf(2.f, fmaf(a.x, a.x, a.y * a.y) + fmaf(b.x, b.x, b.y * b.y), ps);
                 }
             }
+            return ps;
         };
         // empty[b] completes once per use of buffer b: tile i is its (i / kWsBuf)-th use.  All
         // producer threads agree on the outcome (named barrier 2).
@@ -536,11 +557,12 @@ __device__ __forceinline__ void ws_pass_body(float2 *__restrict__ rho, const FPa
             return bar_and(2, WP, mbar_wait(&sm.bars[kWsBuf + i % kWsBuf], (i / kWsBuf) & 1u, wait_limit));
         };
         bool ok = true;
+        double pacc = 0.0;  // this thread's purity sum, tile by tile (FP32 within a tile)
         for (unsigned i = 0; i < ntile; i++) {
             if (i >= kWsBuf) {
                 ok = wait_empty(i - kWsBuf);
                 if (!ok) break;
-                store(i - kWsBuf);
+                pacc += (double)store(i - kWsBuf);
                 bar_sync(2, WP);  // every producer's reads of the buffer precede the new copies into it
             }
             if (!(blockIdx.x == 0 && (int)i == stall_tile)) load(i);
@@ -556,10 +578,16 @@ __device__ __forceinline__ void ws_pass_body(float2 *__restrict__ rho, const FPa
         }
         for (unsigned i = ntile >= kWsBuf ? ntile - kWsBuf : 0; ok && i < ntile; i++) {
             ok = wait_empty(i);
-            if (ok) store(i);
+            if (ok) pacc += (double)store(i);
         }
         cp_async_wait_all();
         if (!ok && tid == WC) atomicOr(err, 1ull);
+        if (pur) {  // fixed order: shuffle tree per warp, then warp 0 + warp 1
+            pacc = warp_sum(pacc);
+            if (lane == 0) sm.psum[pw] = pacc;
+            bar_sync(2, WP);
+            if (tid == WC) purity_part[blockIdx.x] = sm.psum[0] + sm.psum[1];
+        }
         return;
     }
 
@@ -615,22 +643,26 @@ __device__ __forceinline__ void ws_pass_body(float2 *__restrict__ rho, const FPa
     }
 }
 
+template <bool PUR>
 __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
     k_fused_herm_ws(float2 *__restrict__ rho, const FPass *__restrict__ passes, const FPhase *__restrict__ phases,
                     const float2 *__restrict__ coefs, int pass_idx, unsigned npairs,
                     unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile,
-                    const __grid_constant__ WsParams prm)
+                    double *__restrict__ purity_part, const __grid_constant__ WsParams prm)
 {
-    ws_pass_body<false>(rho, passes, phases, coefs, pass_idx, npairs, err, wait_limit, stall_tile, prm);
+    ws_pass_body<false, PUR>(rho, passes, phases, coefs, pass_idx, npairs, err, wait_limit, stall_tile, purity_part,
+                                    prm);
 }
 
+template <bool PUR>
 __global__ void __launch_bounds__(WTH, kWsCtasPerSm)
     k_fused_herm_tc(float2 *__restrict__ rho, const FPass *__restrict__ passes, const FPhase *__restrict__ phases,
                     const float2 *__restrict__ coefs, int pass_idx, unsigned npairs,
                     unsigned long long *__restrict__ err, unsigned wait_limit, int stall_tile,
-                    const __grid_constant__ WsParams prm)
+                    double *__restrict__ purity_part, const __grid_constant__ WsParams prm)
 {
-    ws_pass_body<true>(rho, passes, phases, coefs, pass_idx, npairs, err, wait_limit, stall_tile, prm);
+    ws_pass_body<true, PUR>(rho, passes, phases, coefs, pass_idx, npairs, err, wait_limit, stall_tile, purity_part,
+                                    prm);
 }
 
 static bool herm_kernel(const qcw_ctx *c)
@@ -746,7 +778,9 @@ static int auto_k(const std::vector<QOp> &ops, size_t b, size_t e, int n, bool h
 
 static const size_t kMaxCached = 64;
 
-static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
+// last: nothing follows this segment in the flush, so its last pass (if warp-specialised) also
+// leaves the purity partials of the resulting rho.
+static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e, bool last)
 {
     FusedRuntime *rt = c->fused;
     const int n = c->n;
@@ -818,9 +852,13 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
     qcw_status sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_pass), maxsm);
     if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm), maxsm);
     const bool tc = tc_kernel(c);
-    const void *wsk = tc ? reinterpret_cast<const void *>(k_fused_herm_tc) : reinterpret_cast<const void *>(k_fused_herm_ws);
-    if (!sst) sst = ensure_smem_attr(reinterpret_cast<const void *>(k_fused_herm_ws), ws_smem_bytes());
-    if (!sst && tc) sst = ensure_smem_attr(wsk, ws_smem_bytes());
+    const void *wsk[2][2] = {{reinterpret_cast<const void *>(k_fused_herm_ws<false>),
+                              reinterpret_cast<const void *>(k_fused_herm_ws<true>)},
+                             {reinterpret_cast<const void *>(k_fused_herm_tc<false>),
+                              reinterpret_cast<const void *>(k_fused_herm_tc<true>)}};
+    for (int a = 0; a < 2; a++)
+        for (int pu = 0; pu < 2; pu++)
+            if (!sst && (a == 0 || tc)) sst = ensure_smem_attr(wsk[a][pu], ws_smem_bytes());
     if (sst) return sst;
     unsigned &wgrid = tc ? rt->tc_grid : rt->ws_grid;
     if (!wgrid) {
@@ -829,7 +867,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
         // capped by its kTcCols of the SM's 512 tensor-memory columns per CTA.
         int per_sm = 0;
         cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, reinterpret_cast<const void *>(k_fused_herm_ws), WTH, ws_smem_bytes());
+            &per_sm, reinterpret_cast<const void *>(k_fused_herm_ws<false>), WTH, ws_smem_bytes());
         if (oe != cudaSuccess) return cuda_error(oe, "occupancy");
         if (tc) per_sm = std::min(per_sm, 512 / kTcCols);
         wgrid = (unsigned)std::max(1, per_sm) * (unsigned)c->nsm;
@@ -860,18 +898,32 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
             qcw_status fs = ensure_full(c);  // the other kernels read both triangles
             if (fs) return fs;
         }
+        c->state_ver++;
         if (ws_pass(c, hit->hpass[p])) {
             c->half = true;
             const unsigned npairs = (unsigned)hit->grid[p];
+            double *ppart = nullptr;
+            if (last && p + 1 == hit->hpass.size()) {
+                const int need = (int)std::min(npairs, wgrid);
+                if (rt->ppart_cap < need) {
+                    if (rt->d_ppart) cudaFree(rt->d_ppart);
+                    rt->d_ppart = nullptr;
+                    rt->ppart_cap = 0;
+                    if (cudaMalloc(&rt->d_ppart, sizeof(double) * (size_t)need) != cudaSuccess) {
+                        cudaGetLastError();
+                        return set_error(QCW_ENOMEM, "purity partials");
+                    }
+                    rt->ppart_cap = need;
+                }
+                ppart = rt->d_ppart;
+                rt->ppart_nb = need;
+            }
             const unsigned wl = c->wait_limit ? c->wait_limit : kWsWaitLimit;
-            if (tc)
-                k_fused_herm_tc<<<std::min(npairs, wgrid), WTH, ws_smem_bytes(), c->stream>>>(
-                    c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), wl, c->stall_tile,
-                    hit->prm[hit->prm_idx[p]]);
-            else
-                k_fused_herm_ws<<<std::min(npairs, wgrid), WTH, ws_smem_bytes(), c->stream>>>(
-                    c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), wl, c->stall_tile,
-                    hit->prm[hit->prm_idx[p]]);
+            auto kern = tc ? (ppart ? k_fused_herm_tc<true> : k_fused_herm_tc<false>)
+                           : (ppart ? k_fused_herm_ws<true> : k_fused_herm_ws<false>);
+            kern<<<std::min(npairs, wgrid), WTH, ws_smem_bytes(), c->stream>>>(
+                c->rho, dp, dph, dco, (int)p, npairs, device_error_word(c), wl, c->stall_tile, ppart,
+                hit->prm[hit->prm_idx[p]]);
         } else if (hit->hpass[p].herm) {
             k_fused_herm<<<hit->grid[p], HT, hit->smem[p], c->stream>>>(c->rho, dp, dph, dco, (int)p);
         } else {
@@ -886,6 +938,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e)
         }
         cudaError_t er = cudaGetLastError();
         if (er != cudaSuccess) return cuda_error(er, "fused pass launch");
+        if (last && p + 1 == hit->hpass.size() && ws_pass(c, hit->hpass[p])) c->purity_ver = c->state_ver;
     }
     if (trial) {
         cudaEventRecord(tn.e1, c->stream);
@@ -929,12 +982,21 @@ qcw_status fused_flush(qcw_ctx *c)
             if (!lower_controlled(op) || op.k > 2) barrier = true;
         }
         if (!barrier) continue;
-        if (i > b) st = run_segment(c, b, i);
+        if (i > b) st = run_segment(c, b, i, i == nq);
         if (!st && i < nq) st = plain_apply(c, c->queue[i]);
         b = i + 1;
     }
     c->queue.clear();
     return st;
+}
+
+bool fused_purity_partials(qcw_ctx *c, const double **partials, int *nblocks)
+{
+    FusedRuntime *rt = c->fused;
+    if (!rt || !rt->d_ppart || c->purity_ver != c->state_ver) return false;
+    *partials = rt->d_ppart;
+    *nblocks = rt->ppart_nb;
+    return true;
 }
 
 void fused_collect_timing(qcw_ctx *c)
@@ -959,6 +1021,7 @@ void fused_destroy(qcw_ctx *c)
     FusedRuntime *rt = c->fused;
     if (!rt) return;
     for (CachedPlan &cp : rt->cache) release_plan(cp);
+    if (rt->d_ppart) cudaFree(rt->d_ppart);
     for (cudaEvent_t e : rt->ev_free) cudaEventDestroy(e);
     for (cudaEvent_t e : rt->ev_pending) cudaEventDestroy(e);
     if (rt->tune.e0) cudaEventDestroy(rt->tune.e0);

@@ -520,6 +520,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_purity_lower(const float4 *__re
     block_store<1>(acc, 1, partials);
 }
 
+// out[0] = the sum of nblocks partials (fixed tree).
+void launch_fold(const double *partials, int nblocks, double *out, cudaStream_t s)
+{
+    k_fold<<<1, 32, 0, s>>>(partials, nblocks, 1, out);
+}
+
 void launch_purity_lower(const float2 *rho, int n, double *partials, double *out, int nblocks, cudaStream_t s)
 {
     const uint64_t dim = 1ull << n;

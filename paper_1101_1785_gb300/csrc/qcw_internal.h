@@ -77,6 +77,9 @@ void launch_project(float2 *rho, int n, int qubit, int m, float scale, int nsm, 
 // triangle), and purity from the lower triangle (2 |rho_rc|^2 below the diagonal).
 void launch_symmetrize(float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_purity_lower(const float2 *rho, int n, double *partials, double *out, int nblocks, cudaStream_t s);
+void launch_fold(const double *partials, int nblocks, double *out, cudaStream_t s);
+// The purity partials of the last fused pass, if they describe the current rho.
+bool fused_purity_partials(qcw_ctx *c, const double **partials, int *nblocks);
 void launch_partial_trace(const float2 *rho, const PTParams &p, double2 *out, int nsm,
                           cudaStream_t s);
 int launches_per_reduce();
@@ -125,6 +128,11 @@ struct qcw_ctx {
     // half storage: only the lower triangle (r >= c) of rho is current (the warp-specialised
     // pass leaves it so); ensure_full completes the matrix before anything else reads it
     bool half = false;
+    // Version of rho: bumped by everything that changes it.  The last fused pass of a flush
+    // also sums |rho_rc|^2 over what it writes (per-CTA partials in the fused runtime);
+    // purity_ver records the version those partials describe.
+    unsigned long long state_ver = 1;
+    unsigned long long purity_ver = 0;
     // counters
     long long launches = 0;
     long long passes = 0;

@@ -329,3 +329,40 @@ def test_pass_with_more_phases_than_the_parameter_block_holds(q, kernel):
     assert abs(d.purity() - oracle.purity(want)) <= 1e-6
     assert np.abs(d.get_state() - want).max() <= ATOL
     d.close()
+
+
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_purity_from_the_pass_epilogue(q, kernel):
+    """The last fused pass of a flush also sums w |rho_rc|^2 over the elements it writes (w = 2
+    below the diagonal, 1 on it).  That purity matches the oracle and the standalone reduction
+    (taken after direct device access invalidates the pass's sums), is bitwise reproducible,
+    and is not reused once the state changes (gate, measurement)."""
+    n = 10
+    c = wl.random_circuit(n, 60, 6100 + kernel, "mixed", "adpd")
+    want = oracle.run_circuit(c)
+    vals = []
+    for _ in range(2):
+        d = q.Density(n)
+        d.set_mode(q.QCW_MODE_FUSED, 5)
+        d.set_fused_kernel(kernel)
+        for op in c.ops:
+            d.apply_op(op)
+        vals.append(d.purity())
+        d.device_state()  # the caller may write rho: the pass's sums no longer count
+        standalone = d.purity()
+        assert abs(standalone - vals[-1]) <= 1e-6
+        d.close()
+    assert vals[0] == vals[1]
+    assert abs(vals[0] - oracle.purity(want)) <= 1e-6
+    # a state change after the pass: the next purity comes from the new state
+    d = q.Density(n)
+    d.set_mode(q.QCW_MODE_FUSED, 5)
+    d.set_fused_kernel(kernel)
+    for op in c.ops:
+        d.apply_op(op)
+    d.trace()  # flushes; the pass's sums describe rho
+    m_ref, _ = oracle.measure(want, 2, 1)
+    m, _ = d.measure(2, 1)
+    assert m == m_ref
+    assert abs(d.purity() - oracle.purity(want)) <= 1e-6
+    d.close()
