@@ -143,6 +143,11 @@ def test_planner_replay_matches_oracle(shim, n, kmax, seed, search):
             oracle.apply_kraus(want, np.stack(m), qs)
     phases, pass_nq = _plan(shim, n, kmax, ops, search)
     assert (pass_nq <= kmax).all() and len(pass_nq) >= 1
+    assert np.abs(_replay(phases, n, rho0) - want).max() < 1e-12
+
+
+def _replay(phases, n, rho0):
+    """The planned phases applied in order with numpy."""
     got = rho0.copy()
     for _, nq, (qa, qb), product, S in phases:
         if nq == 1:
@@ -152,7 +157,65 @@ def test_planner_replay_matches_oracle(shim, n, kmax, seed, search):
             got = _apply_superop(got, n, S[16:32], (qb,))
         else:
             got = _apply_superop(got, n, S, (qa, qb))
-    assert np.abs(got - want).max() < 1e-12
+    return got
+
+
+def _oracle_run(ops, rho0):
+    want = rho0.copy()
+    for kind, qs, m in ops:
+        if kind == "u":
+            oracle.apply_unitary(want, m, qs)
+        else:
+            oracle.apply_kraus(want, np.stack(m), qs)
+    return want
+
+
+def _structure(phases):
+    return [(nq, q if nq == 2 else (q[0],), prod) for _, nq, q, prod, _ in phases]
+
+
+def test_phases_anchor_on_two_qubit_operations(shim):
+    """A two-qubit operation opens a phase that takes the single-qubit operations on its qubits
+    placed so far; later single-qubit operations and a second operation on the same pair join
+    it; a qubit with no two-qubit operation in the pass gets its own phase, placed first."""
+    rng = np.random.default_rng(5)
+    ops = [("u", (0,), haar_unitary(rng, 2)), ("u", (2,), haar_unitary(rng, 2)),
+           ("u", (0, 1), haar_unitary(rng, 4)), ("u", (0,), haar_unitary(rng, 2)),
+           ("k", (1,), [np.sqrt(w) * haar_unitary(rng, 2) for w in (0.6, 0.4)]),
+           ("u", (1, 0), haar_unitary(rng, 4)), ("u", (1,), haar_unitary(rng, 2))]
+    phases, pass_nq = _plan(shim, 3, 3, ops)
+    assert len(pass_nq) == 1
+    assert _structure(phases) == [(1, (2,), False), (2, (0, 1), False)]
+    rho0 = random_rho(rng, 3)
+    assert np.abs(_replay(phases, 3, rho0) - _oracle_run(ops, rho0)).max() < 1e-12
+
+
+def test_single_qubit_operation_joins_the_last_phase_on_its_qubit(shim):
+    """After phases on (0, 1) and (1, 2), an operation on qubit 0 commutes past the (1, 2) phase
+    into the (0, 1) one and an operation on qubit 1 joins (1, 2); a two-qubit operation on (0, 2)
+    whose qubits' last phases differ opens a new phase."""
+    rng = np.random.default_rng(6)
+    ops = [("u", (0, 1), haar_unitary(rng, 4)), ("u", (1, 2), haar_unitary(rng, 4)),
+           ("u", (0,), haar_unitary(rng, 2)), ("u", (1,), haar_unitary(rng, 2)),
+           ("u", (0, 2), haar_unitary(rng, 4)), ("u", (2,), haar_unitary(rng, 2))]
+    phases, pass_nq = _plan(shim, 3, 3, ops)
+    assert len(pass_nq) == 1
+    assert _structure(phases) == [(2, (0, 1), False), (2, (1, 2), False), (2, (0, 2), False)]
+    rho0 = random_rho(rng, 3)
+    assert np.abs(_replay(phases, 3, rho0) - _oracle_run(ops, rho0)).max() < 1e-12
+
+
+def test_qubits_without_two_qubit_operations_pair_into_product_phases(shim):
+    """Five qubits with single-qubit operations only: product phases on (0, 1) and (2, 3) and a
+    one-qubit phase on 4, whatever the order of the operations."""
+    rng = np.random.default_rng(7)
+    ops = [("u", (q,), haar_unitary(rng, 2)) for q in (4, 2, 0, 3, 1, 0, 4, 2)]
+    ops.append(("k", (3,), [np.sqrt(w) * haar_unitary(rng, 2) for w in (0.5, 0.5)]))
+    phases, pass_nq = _plan(shim, 5, 5, ops)
+    assert len(pass_nq) == 1
+    assert _structure(phases) == [(2, (0, 1), True), (2, (2, 3), True), (1, (4,), False)]
+    rho0 = random_rho(rng, 5)
+    assert np.abs(_replay(phases, 5, rho0) - _oracle_run(ops, rho0)).max() < 1e-12
 
 
 def test_planner_packs_disjoint_work(shim):
