@@ -193,7 +193,12 @@ QCW_API qcw_status qcw_sync(qcw_ctx *ctx);
 /* Tr rho = sum_i rho_ii (FP64).  Synchronises. */
 QCW_API qcw_status qcw_trace(qcw_ctx *ctx, double *re, double *im);
 
-/* sum_ij |rho_ij|^2, which equals Tr[rho . rho] (Sec. 5.2.3) for Hermitian rho (FP64). */
+/* sum_ij |rho_ij|^2, which equals Tr[rho . rho] (Sec. 5.2.3) for Hermitian rho (FP64).
+ * Flushes queued work first.  When the last fused pass of the latest flush was a HERM_WS /
+ * HERM_TC pass and nothing has changed rho since, the value comes from sums that pass took
+ * over its write-back (squares in FP32 within a tile, FP64 above; no extra read of rho);
+ * otherwise rho is read.  Either way the summation order is fixed (reproducible bit for bit).
+ * Synchronises. */
 QCW_API qcw_status qcw_purity(qcw_ctx *ctx, double *out);
 
 /* p1_out[i] = sum over labels r with qubit i equal to 1 of Re rho_rr, i = 0..n-1 (FP64). */
