@@ -672,8 +672,9 @@ static bool herm_kernel(const qcw_ctx *c)
 }
 
 // The warp-specialised pass with its two-qubit phases on the tensor cores.  Not the default:
-// on GB300 it runs the 14-qubit benchmark's passes at 1.18 ms against 1.14 ms on the CUDA cores
-// (each phase's MMA round trip is a latency chain that two CTAs per SM cannot hide).
+// on GB300 it runs the 14-qubit benchmark's passes about 4 % slower than the CUDA-core kernel
+// (1.049 against 1.006 ms: each phase's MMA round trip is a latency chain that two CTAs per SM
+// cannot hide).
 static bool tc_kernel(const qcw_ctx *c) { return c->fused_kernel == QCW_FUSED_KERNEL_HERM_TC; }
 
 // Passes the warp-specialised kernel takes: Hermitian, 2^12-element tiles with column bit 0 of
