@@ -172,10 +172,17 @@ TIMED_KERNEL = {"auto": "k_fused_herm_ws", "herm_tc": "k_fused_herm_tc", "herm_w
 
 
 def kernel_hash():
+    """Hash of the pass kernel's sources with comments and whitespace removed, so that a
+    recorded measurement stays attached to the code it measured."""
+    import re
+
     h = hashlib.sha256()
     for f in ("fused.cu", "planner.cpp", "qcw_device.cuh", "tile.cuh", "tile.cpp", "tc.cuh"):
-        with open(os.path.join(ROOT, "paper_1101_1785_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1101_1785_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
