@@ -134,10 +134,13 @@ def gpu_step(d, packed, host_rho_ptr=None, loaded=False):
         d.reset()
     else:
         d.set_state_c64(host_rho_ptr)
-    tp = []
+    # trace and purity every CHUNK gates as asynchronous checkpoints: the host queues and plans
+    # the next chunk while the GPU evolves this one
+    tickets = []
     for p in packed:
         d.apply_packed(p)
-        tp.append((d.trace(), d.purity()))
+        tickets.append(d.checkpoint())
+    tp = [(tr, pu) for tr, pu, _ in (d.checkpoint_read(t) for t in tickets)]
     probs = d.probabilities()
     m, pm = d.measure(0, -1, U_MEASURE)
     pt = d.partial_trace(PT_KEEP)
@@ -145,8 +148,9 @@ def gpu_step(d, packed, host_rho_ptr=None, loaded=False):
 
 
 def d2h_bytes_per_step(n):
-    diag = (n + 2) * 8
-    return (N_GATES // CHUNK) * (diag + 8) + diag + diag + 16 * (4 ** len(PT_KEEP))
+    """Checkpoint slots ((n + 3) values and the error word per checkpoint), the 64-double result
+    block of the probabilities and the measurement readouts, and the partial trace."""
+    return (N_GATES // CHUNK) * (n + 4) * 8 + 2 * 64 * 8 + 16 * (4 ** len(PT_KEEP))
 
 
 def pass_unit_bytes(n):

@@ -204,6 +204,22 @@ QCW_API qcw_status qcw_purity(qcw_ctx *ctx, double *out);
 /* p1_out[i] = sum over labels r with qubit i equal to 1 of Re rho_rr, i = 0..n-1 (FP64). */
 QCW_API qcw_status qcw_probabilities(qcw_ctx *ctx, double *p1_out);
 
+/* Asynchronous readout of the trace, purity and probabilities (the values of qcw_trace,
+ * qcw_purity and qcw_probabilities, same arithmetic) at this point of the evolution, e.g.
+ * every 100 gates as in the paper's noise studies (Sec. 5.2.3).  The paper has no asynchronous
+ * form; it lets the host queue and plan the next operations while the GPU works.
+ * qcw_checkpoint flushes queued work, enqueues the FP64 reductions and their copy to pinned
+ * host memory on the context's stream, and returns at once with *ticket (0, 1, 2, ... per
+ * context).  qcw_checkpoint_read waits for checkpoint `ticket` and writes
+ *   out[0] = Re tr rho, out[1] = Im tr rho, out[2 + q] = P(qubit q = 1) for q < n,
+ *   out[2 + n] = purity
+ * (n + 3 doubles, caller-owned).  Results are kept for the last QCW_CHECKPOINT_SLOTS
+ * checkpoints; reading an older or a future ticket returns QCW_EINVAL.  A fused pass whose
+ * in-kernel wait ran out before the checkpoint makes the read return QCW_ETIMEOUT. */
+#define QCW_CHECKPOINT_SLOTS 64
+QCW_API qcw_status qcw_checkpoint(qcw_ctx *ctx, long long *ticket);
+QCW_API qcw_status qcw_checkpoint_read(qcw_ctx *ctx, long long ticket, double *out);
+
 /* Projective measurement of `qubit` (the ancilla read-out of Sec. 5.4.1; textbook form):
  * p_m = sum_{r: q(r) = m} Re rho_rr; the outcome m is `forced` when it is 0 or 1,
  * otherwise m = 0 iff u < p_0 (u: caller's uniform draw in [0, 1)).  Then

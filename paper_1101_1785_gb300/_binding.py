@@ -57,6 +57,8 @@ SIGNATURES = {
     "qcw_trace": (I, [P, PD, PD]),
     "qcw_purity": (I, [P, PD]),
     "qcw_probabilities": (I, [P, P]),
+    "qcw_checkpoint": (I, [P, PLL]),
+    "qcw_checkpoint_read": (I, [P, LL, P]),
     "qcw_measure": (I, [P, I, I, D, PI, PD]),
     "qcw_partial_trace": (I, [P, P, I, P]),
     "qcw_partial_trace_static": (I, [P, I, P, I, P, P]),
@@ -301,6 +303,19 @@ class Density:
         out = np.zeros(self.n, dtype=np.float64)
         check(lib().qcw_probabilities(self.h, _p(out)), "qcw_probabilities")
         return out
+
+    def checkpoint(self) -> int:
+        """Enqueue the trace / purity / probability reductions of the current rho (flushes queued
+        work, does not wait); returns the ticket for checkpoint_read."""
+        t = LL()
+        check(lib().qcw_checkpoint(self.h, ctypes.byref(t)), "qcw_checkpoint")
+        return t.value
+
+    def checkpoint_read(self, ticket: int):
+        """(trace, purity, probabilities) of checkpoint `ticket` (waits for it)."""
+        out = np.zeros(self.n + 3, dtype=np.float64)
+        check(lib().qcw_checkpoint_read(self.h, int(ticket), _p(out)), "qcw_checkpoint_read")
+        return complex(out[0], out[1]), float(out[2 + self.n]), out[2:2 + self.n].copy()
 
     def measure(self, qubit: int, forced: int = -1, u: float = 0.0):
         oc, pr = I(), D()

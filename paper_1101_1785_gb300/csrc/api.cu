@@ -247,6 +247,10 @@ static void ctx_free(qcw_ctx *c)
     if (c->d_result) cudaFree(c->d_result);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->d_staging) cudaFree(c->d_staging);
+    if (c->d_ckpt) cudaFree(c->d_ckpt);
+    if (c->h_ckpt) cudaFreeHost(c->h_ckpt);
+    for (cudaEvent_t e : c->ckpt_ev)
+        if (e) cudaEventDestroy(e);
     if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -674,6 +678,78 @@ extern "C" qcw_status qcw_purity(qcw_ctx *ctx, double *out)
     st = fetch_results(ctx);
     if (st) return st;
     *out = ctx->h_result[0];
+    return QCW_OK;
+}
+
+// ------------------------------------------------------------------ asynchronous readouts
+// Slot layout: Re tr, Im tr, P(q = 1) for q < QCW_MAX_QUBITS (n used), purity at 2 + n, and the
+// context's error word in the last entry.
+static const int kCkptVals = QCW_MAX_QUBITS + 4;
+
+extern "C" qcw_status qcw_checkpoint(qcw_ctx *ctx, long long *ticket)
+{
+    CHECK_CTX(ctx);
+    if (!ticket) return set_error(QCW_EINVAL, "null ticket");
+    if (!ctx->d_ckpt) {
+        const size_t bytes = sizeof(double) * QCW_CHECKPOINT_SLOTS * kCkptVals;
+        if (cudaMalloc(&ctx->d_ckpt, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->d_ckpt = nullptr;
+            return set_error(QCW_ENOMEM, "checkpoint slots");
+        }
+        if (cudaMallocHost(&ctx->h_ckpt, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_ckpt = nullptr;
+            return set_error(QCW_ENOMEM, "pinned checkpoint slots");
+        }
+        for (int i = 0; i < QCW_CHECKPOINT_SLOTS; i++) {
+            ctx->ckpt_ticket[i] = -1;
+            CK(cudaEventCreateWithFlags(&ctx->ckpt_ev[i], cudaEventDisableTiming));
+        }
+    }
+    qcw_status st = fused_flush(ctx);
+    if (st) return st;
+    const long long t = ctx->ckpt_next;
+    const int slot = (int)(t % QCW_CHECKPOINT_SLOTS);
+    double *d = ctx->d_ckpt + (size_t)slot * kCkptVals;
+    double *h = ctx->h_ckpt + (size_t)slot * kCkptVals;
+    const int n = ctx->n;
+    launch_diag_reduce(ctx->rho, n, ctx->d_partials, d, ctx->red_blocks, ctx->stream);
+    CKLAUNCH(ctx, launches_per_reduce());
+    const double *part = nullptr;
+    int nb = 0;
+    if (fused_purity_partials(ctx, &part, &nb)) {
+        launch_fold(part, nb, d + 2 + n, ctx->stream);
+        CKLAUNCH(ctx, 1);
+    } else {
+        if (ctx->half) launch_purity_lower(ctx->rho, n, ctx->d_partials, d + 2 + n, ctx->red_blocks, ctx->stream);
+        else launch_purity(ctx->rho, n, ctx->d_partials, d + 2 + n, ctx->red_blocks, ctx->stream);
+        CKLAUNCH(ctx, launches_per_reduce());
+    }
+    CK(cudaMemcpyAsync(h, d, sizeof(double) * (size_t)(n + 3), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(h + kCkptVals - 1, device_error_word(ctx), sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaEventRecord(ctx->ckpt_ev[slot], ctx->stream));
+    ctx->ckpt_ticket[slot] = t;
+    ctx->ckpt_next = t + 1;
+    *ticket = t;
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_checkpoint_read(qcw_ctx *ctx, long long ticket, double *out)
+{
+    CHECK_CTX(ctx);
+    if (!out) return set_error(QCW_EINVAL, "null output");
+    if (ticket < 0 || ticket >= ctx->ckpt_next || !ctx->d_ckpt) return set_error(QCW_EINVAL, "unknown checkpoint");
+    const int slot = (int)(ticket % QCW_CHECKPOINT_SLOTS);
+    if (ctx->ckpt_ticket[slot] != ticket) return set_error(QCW_EINVAL, "checkpoint overwritten");
+    CK(cudaEventSynchronize(ctx->ckpt_ev[slot]));
+    const double *h = ctx->h_ckpt + (size_t)slot * kCkptVals;
+    unsigned long long w;
+    memcpy(&w, h + kCkptVals - 1, sizeof w);
+    qcw_status st = check_error_word(ctx, w);
+    if (st) return st;
+    memcpy(out, h, sizeof(double) * (size_t)(ctx->n + 3));
     return QCW_OK;
 }
 

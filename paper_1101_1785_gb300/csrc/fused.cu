@@ -59,6 +59,7 @@ struct CachedPlan {
     std::vector<int> grid;  // tiles per pass
     std::vector<size_t> smem;
     char *dbuf = nullptr;  // device copy of passes | phases | coefs
+    char *hbuf = nullptr;  // its pinned host source (the upload is stream-ordered)
     std::vector<WsParams> prm;  // parameter blocks of the warp-specialised kernel's passes
     std::vector<int> prm_idx;   // per pass: index into prm, -1 if the pass has none
     size_t phase_off = 0, coef_off = 0;
@@ -111,13 +112,16 @@ struct FusedRuntime {
     KTune tune;
 };
 
-// Collect a finished trial; returns true while the trial is still running.
+// Collect the pending trial, waiting for it: until the choice is made the host keeps pace with
+// the timed segments (otherwise, with readouts that do not synchronise, the host would run
+// whole steps ahead and the undecided widths would keep building plans).  Returns false.
 static bool tune_poll(KTune &t)
 {
     if (!t.pending) return false;
-    if (cudaEventQuery(t.e1) != cudaSuccess) {
+    if (cudaEventSynchronize(t.e1) != cudaSuccess) {
         cudaGetLastError();
-        return true;
+        t.pending = false;
+        return false;
     }
     float ms = 0;
     if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess && t.nops) {
@@ -724,25 +728,35 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
     size_t sz_ph = sizeof(FPhase) * tp.phases.size();
     cp.coef_off = (cp.phase_off + sz_ph + 255) & ~(size_t)255;
     size_t total = cp.coef_off + sizeof(float2) * tp.coefs.size();
-    std::vector<char> host(total, 0);
-    memcpy(host.data(), tp.passes.data(), sz_pass);
-    if (sz_ph) memcpy(host.data() + cp.phase_off, tp.phases.data(), sz_ph);
-    if (!tp.coefs.empty()) memcpy(host.data() + cp.coef_off, tp.coefs.data(), sizeof(float2) * tp.coefs.size());
+    if (cudaMallocHost(&cp.hbuf, total) != cudaSuccess) {
+        cudaGetLastError();
+        cp.hbuf = nullptr;
+        return set_error(QCW_ENOMEM, "fused plan staging");
+    }
+    memset(cp.hbuf, 0, total);
+    memcpy(cp.hbuf, tp.passes.data(), sz_pass);
+    if (sz_ph) memcpy(cp.hbuf + cp.phase_off, tp.phases.data(), sz_ph);
+    if (!tp.coefs.empty()) memcpy(cp.hbuf + cp.coef_off, tp.coefs.data(), sizeof(float2) * tp.coefs.size());
     if (cudaMalloc(&cp.dbuf, total) != cudaSuccess) {
         cudaGetLastError();
         cp.dbuf = nullptr;
         return set_error(QCW_ENOMEM, "fused plan buffer");
     }
-    // synchronous copy: the host vector dies at return
-    cudaError_t er = cudaMemcpy(cp.dbuf, host.data(), total, cudaMemcpyHostToDevice);
+    // ordered before the passes that read it on the same stream, and not with other streams'
+    // work (a plain cudaMemcpy would wait for the whole device)
+    cudaError_t er = cudaMemcpyAsync(cp.dbuf, cp.hbuf, total, cudaMemcpyHostToDevice, c->stream);
     if (er != cudaSuccess) return cuda_error(er, "fused plan upload");
     return QCW_OK;
 }
 
+// Callers make sure no work on the context's stream still uses the plan (eviction synchronises
+// the stream first; contexts synchronise before destruction).
 static void release_plan(CachedPlan &cp)
 {
     if (cp.dbuf) cudaFree(cp.dbuf);
+    if (cp.hbuf) cudaFreeHost(cp.hbuf);
     cp.dbuf = nullptr;
+    cp.hbuf = nullptr;
 }
 
 // Fusion width for the fused path: the candidate with the lowest modeled time.  The model

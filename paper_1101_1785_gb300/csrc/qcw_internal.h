@@ -133,6 +133,13 @@ struct qcw_ctx {
     // purity_ver records the version those partials describe.
     unsigned long long state_ver = 1;
     unsigned long long purity_ver = 0;
+    // asynchronous readouts: QCW_CHECKPOINT_SLOTS slots of kCkptVals doubles on the device and
+    // in pinned host memory, the ticket each slot holds and an event marking its copy
+    double *d_ckpt = nullptr;
+    double *h_ckpt = nullptr;
+    long long ckpt_ticket[QCW_CHECKPOINT_SLOTS];
+    cudaEvent_t ckpt_ev[QCW_CHECKPOINT_SLOTS] = {};
+    long long ckpt_next = 0;
     // counters
     long long launches = 0;
     long long passes = 0;

@@ -366,3 +366,78 @@ def test_purity_from_the_pass_epilogue(q, kernel):
     assert m == m_ref
     assert abs(d.purity() - oracle.purity(want)) <= 1e-6
     d.close()
+
+
+@pytest.mark.parametrize("mode,kernel", [("fused", 3), ("fused", 4), ("plain", 0)])
+def test_checkpoints_match_synchronous_readouts(q, mode, kernel):
+    """Asynchronous checkpoints after each third of a circuit hold exactly the values the
+    synchronous readouts give on an identical context at the same points (same kernels, same
+    summation order), and the last one matches the oracle."""
+    n = 9
+    c = wl.random_circuit(n, 90, 7300 + kernel, "mixed", "adpd")
+    ctxs = []
+    for _ in range(2):
+        d = q.Density(n)
+        if mode == "fused":
+            d.set_mode(q.QCW_MODE_FUSED, 5)
+            d.set_fused_kernel(kernel)
+        ctxs.append(d)
+    d, ref = ctxs
+    thirds = np.array_split(np.arange(len(c.ops)), 3)
+    tickets, want = [], []
+    for part in thirds:
+        for i in part:
+            d.apply_op(c.ops[i])
+            ref.apply_op(c.ops[i])
+        tickets.append(d.checkpoint())
+        want.append((ref.trace(), ref.purity(), ref.probabilities()))
+    for t, (tr, pu, pr) in zip(tickets, want):
+        gtr, gpu, gpr = d.checkpoint_read(t)
+        assert gtr == tr and gpu == pu
+        np.testing.assert_array_equal(gpr, pr)
+    rho = oracle.run_circuit(c)
+    gtr, gpu, gpr = d.checkpoint_read(tickets[-1])
+    assert abs(gtr - oracle.trace(rho)) <= TRACE_TOL
+    assert abs(gpu - oracle.purity(rho)) <= 1e-6
+    np.testing.assert_allclose(gpr, oracle.probabilities(rho), atol=1e-6, rtol=0)
+    d.close()
+    ref.close()
+
+
+def test_checkpoint_tickets(q):
+    """Unknown and future tickets are rejected; the ring keeps the last QCW_CHECKPOINT_SLOTS."""
+    d = q.Density(3)
+    with pytest.raises(q.QcwError) as e:
+        d.checkpoint_read(0)
+    assert e.value.status == q.QCW_EINVAL
+    tickets = [d.checkpoint() for _ in range(65)]
+    assert tickets == list(range(65))
+    with pytest.raises(q.QcwError) as e:
+        d.checkpoint_read(0)
+    assert e.value.status == q.QCW_EINVAL
+    with pytest.raises(q.QcwError) as e:
+        d.checkpoint_read(65)
+    assert e.value.status == q.QCW_EINVAL
+    tr, pu, pr = d.checkpoint_read(64)
+    assert tr == 1.0 and pu == 1.0 and (pr == 0.0).all()
+    d.close()
+
+
+def test_checkpoint_reports_a_wait_that_ran_out(q):
+    """A fused pass whose bounded wait ran out before the checkpoint: the read returns
+    QCW_ETIMEOUT (the error word travels with the checkpoint's values)."""
+    n = 9
+    c = wl.random_circuit(n, 40, 4041, "mixed", "adpd")
+    d = q.Density(n)
+    d.set_mode(q.QCW_MODE_FUSED, 4)
+    d.set_fused_kernel(3)
+    d.set_fused_wait_limit(2000, 0)
+    for op in c.ops:
+        d.apply_op(op)
+    t = d.checkpoint()
+    with pytest.raises(q.QcwError) as e:
+        d.checkpoint_read(t)
+    assert e.value.status == q.QCW_ETIMEOUT
+    d.set_fused_wait_limit(0, -1)
+    d.reset()
+    d.close()
