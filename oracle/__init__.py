@@ -64,9 +64,10 @@ def _load():
             lib.orc_probabilities.restype = None
             lib.orc_measure.argtypes = [P, I, I, I, D, P, P]
             lib.orc_partial_trace.argtypes = [P, I, P, I, P]
+            lib.orc_pauli_expectation.argtypes = [P, I, P, P, I, P]
             lib.orc_set_threads.argtypes = [I]
             for f in ("orc_apply_unitary", "orc_apply_kraus", "orc_apply_vec", "orc_measure",
-                      "orc_partial_trace", "orc_set_threads"):
+                      "orc_partial_trace", "orc_pauli_expectation", "orc_set_threads"):
                 getattr(lib, f).restype = I
             _lib = lib
     return _lib
@@ -162,6 +163,26 @@ def partial_trace(rho: np.ndarray, keep) -> np.ndarray:
     _check(_load().orc_partial_trace(_ptr(rho), nqubits_of(rho), _ptr(keep), len(keep), _ptr(out)),
            "partial_trace")
     return out
+
+
+def pauli_expectation(rho: np.ndarray, qubits, paulis) -> complex:
+    """Tr[P rho], P the Pauli string sigma_{paulis[j]} on qubits[j] (1 = X, 2 = Y, 3 = Z)."""
+    q, p = _ints(qubits), _ints(paulis)
+    out = np.zeros(2, dtype=np.float64)
+    _check(_load().orc_pauli_expectation(_ptr(rho), nqubits_of(rho), _ptr(q), _ptr(p), len(q), _ptr(out)),
+           "pauli_expectation")
+    return complex(out[0], out[1])
+
+
+def polarization(rho: np.ndarray) -> np.ndarray:
+    """Polarisation vectors P_q = Tr[sigma^(q) rho] (Sec. 5.2), shape (n, 3)."""
+    n = nqubits_of(rho)
+    return np.array([[pauli_expectation(rho, [q], [i]).real for i in (1, 2, 3)] for q in range(n)])
+
+
+def correlation(rho: np.ndarray, q1: int, q2: int) -> np.ndarray:
+    """Spin correlation tensor C_ij = Tr[sigma_i^(q1) sigma_j^(q2) rho] (Sec. 5.2), shape (3, 3)."""
+    return np.array([[pauli_expectation(rho, [q1, q2], [i, j]).real for j in (1, 2, 3)] for i in (1, 2, 3)])
 
 
 def initial_state(circuit) -> np.ndarray:

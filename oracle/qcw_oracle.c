@@ -276,6 +276,45 @@ int orc_partial_trace(const double *rho, int n, const int *keep, int nkeep, doub
     return ORC_OK;
 }
 
+// One Pauli matrix entry sigma_p[a][b] (p = 0: identity).
+static cplx pauli_entry(int p, int a, int b)
+{
+    switch (p) {
+    case 0: return a == b ? 1.0 : 0.0;
+    case 1: return a != b ? 1.0 : 0.0;
+    case 2: return a == b ? 0.0 : (a == 0 ? -I : I);
+    case 3: return a == b ? (a == 0 ? 1.0 : -1.0) : 0.0;
+    }
+    return 0.0;
+}
+
+int orc_pauli_expectation(const double *rho, int n, const int *qubits, const int *paulis, int k, double *out)
+{
+    if (n < 1 || k < 0 || k > n) return ORC_EINVAL;
+    int pq[32] = {0};  // Pauli index per qubit
+    for (int j = 0; j < k; j++) {
+        if (qubits[j] < 0 || qubits[j] >= n || paulis[j] < 1 || paulis[j] > 3) return ORC_EINVAL;
+        if (pq[qubits[j]]) return ORC_EINVAL;
+        pq[qubits[j]] = paulis[j];
+    }
+    long dim = 1L << n;
+    const cplx *p = (const cplx *)rho;
+    cplx s = 0;
+    // Tr[P rho] = sum_r sum_c P[r][c] rho[c][r], P[r][c] the product over qubits of sigma[r_q][c_q]
+    for (long r = 0; r < dim; r++)
+        for (long c = 0; c < dim; c++) {
+            cplx f = 1.0;
+            for (int q = 0; q < n && f != 0.0; q++) {
+                const long st = orc_stride(n, q);
+                f *= pauli_entry(pq[q], (r & st) != 0, (c & st) != 0);
+            }
+            if (f != 0.0) s += f * p[c * dim + r];
+        }
+    out[0] = creal(s);
+    out[1] = cimag(s);
+    return ORC_OK;
+}
+
 int orc_set_threads(int nthreads)
 {
 #ifdef _OPENMP

@@ -19,6 +19,10 @@ double orc_purity(const double *rho, int n);
 void orc_probabilities(const double *rho, int n, double *p1);
 int orc_measure(double *rho, int n, int qubit, int forced, double u, int *outcome, double *prob);
 int orc_partial_trace(const double *rho, int n, const int *keep, int nkeep, double *out);
+/* Tr[P rho] for the Pauli string P = (x)_j sigma_{paulis[j]} on qubits[j] (1 = X, 2 = Y, 3 = Z;
+ * distinct qubits), identity elsewhere: the polarisation vectors and spin correlation tensor
+ * of Sec. 5.2 are such traces.  out = {Re, Im}. */
+int orc_pauli_expectation(const double *rho, int n, const int *qubits, const int *paulis, int k, double *out);
 int orc_set_threads(int nthreads);
 
 #endif

@@ -360,3 +360,63 @@ def test_invalid_inputs():
         oracle.apply_unitary(rho, np.eye(4), [1, 1])
     with pytest.raises(oracle.OracleError):
         oracle.apply_kraus(rho, np.zeros((0, 2, 2)), [0])
+
+
+def _sigma(i):
+    return [np.eye(2), np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]),
+            np.array([[1, 0], [0, -1]])][i]
+
+
+def test_polarization_of_the_axis_states():
+    """|0>, |1>, |+> = H|0> and |+i> = S H|0> point along +z, -z, +x and +y (Sec. 5.2's
+    one-qubit form rho = (1 + P . sigma) / 2); the Y sign is fixed by |+i>."""
+    cases = [((), (0, 0, 1)), (("X",), (0, 0, -1)), (("H",), (1, 0, 0)), (("H", "S"), (0, 1, 0))]
+    for gates, want in cases:
+        rho = _zero(1)
+        for g in gates:
+            oracle.apply_unitary(rho, wl.gate_matrix(g), [0])
+        np.testing.assert_allclose(oracle.polarization(rho)[0], want, atol=1e-15)
+
+
+def test_polarization_and_correlation_recover_the_pauli_form():
+    """rho = (1 + P1 . sigma x 1 + P2 . 1 x sigma + sum_ij C_ij sigma_i x sigma_j) / 4 with
+    random real coefficients: the traces return P1, P2 and C (the two-qubit form of Sec. 5.2);
+    a one-qubit rho = (1 + P . sigma) / 2 returns P."""
+    rng = np.random.default_rng(31)
+    p = rng.uniform(-0.5, 0.5, 3)
+    rho1 = (np.eye(2) + sum(p[i] * _sigma(i + 1) for i in range(3))) / 2
+    np.testing.assert_allclose(oracle.polarization(rho1.astype(np.complex128))[0], p, atol=1e-15)
+    p1, p2 = rng.uniform(-0.3, 0.3, 3), rng.uniform(-0.3, 0.3, 3)
+    c = rng.uniform(-0.3, 0.3, (3, 3))
+    rho = np.eye(4, dtype=np.complex128)
+    for i in range(3):
+        rho += p1[i] * np.kron(_sigma(i + 1), np.eye(2)) + p2[i] * np.kron(np.eye(2), _sigma(i + 1))
+        for j in range(3):
+            rho += c[i, j] * np.kron(_sigma(i + 1), _sigma(j + 1))
+    rho /= 4
+    pol = oracle.polarization(rho)
+    np.testing.assert_allclose(pol[0], p1, atol=1e-15)
+    np.testing.assert_allclose(pol[1], p2, atol=1e-15)
+    np.testing.assert_allclose(oracle.correlation(rho, 0, 1), c, atol=1e-15)
+    np.testing.assert_allclose(oracle.correlation(rho, 1, 0), c.T, atol=1e-15)
+
+
+def test_bell_state_correlations():
+    """(|00> + |11>)/sqrt 2: no polarisation, correlation tensor diag(1, -1, 1)."""
+    rho = _zero(2)
+    oracle.apply_unitary(rho, wl.gate_matrix("H"), [0])
+    oracle.apply_unitary(rho, wl.gate_matrix("CNOT"), [0, 1])
+    np.testing.assert_allclose(oracle.polarization(rho), np.zeros((2, 3)), atol=1e-15)
+    np.testing.assert_allclose(oracle.correlation(rho, 0, 1), np.diag([1.0, -1.0, 1.0]), atol=1e-15)
+
+
+def test_polarization_of_a_product_state():
+    """rho_a (x) rho_b (x) rho_c: each qubit's vector is its factor's (numpy Bloch vector), and
+    the correlation of qubits 0 and 2 is the outer product of theirs."""
+    rng = np.random.default_rng(32)
+    f = [random_rho(rng, 1) for _ in range(3)]
+    rho = np.kron(np.kron(f[0], f[1]), f[2]).astype(np.complex128)
+    pol = oracle.polarization(rho)
+    for q in range(3):
+        np.testing.assert_allclose(pol[q], bloch(f[q]), atol=1e-14)
+    np.testing.assert_allclose(oracle.correlation(rho, 0, 2), np.outer(bloch(f[0]), bloch(f[2])), atol=1e-14)
