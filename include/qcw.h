@@ -204,6 +204,17 @@ QCW_API qcw_status qcw_purity(qcw_ctx *ctx, double *out);
 /* p1_out[i] = sum over labels r with qubit i equal to 1 of Re rho_rr, i = 0..n-1 (FP64). */
 QCW_API qcw_status qcw_probabilities(qcw_ctx *ctx, double *p1_out);
 
+/* Polarisation vectors (Sec. 5.2: the one-qubit form rho = (1 + P . sigma) / 2 with
+ * P = Tr[sigma rho]): out[3 q + i] = Tr[sigma_i^(q) rho] for qubit q < n and i = 0, 1, 2 for
+ * x, y, z (3 n doubles, caller-owned; FP64 sums of the FP32 elements).  Reads the lower
+ * triangle only.  Flushes queued work first; synchronises. */
+QCW_API qcw_status qcw_polarization(qcw_ctx *ctx, double *out);
+
+/* Spin correlation tensor of qubits q1 != q2 (Sec. 5.2's two-qubit form):
+ * out[3 i + j] = Tr[sigma_i^(q1) sigma_j^(q2) rho], i, j = x, y, z (9 doubles).  QCW_EINVAL for
+ * equal or out-of-range qubits.  Flushes queued work first; synchronises. */
+QCW_API qcw_status qcw_correlation(qcw_ctx *ctx, int q1, int q2, double *out);
+
 /* Asynchronous readout of the trace, purity and probabilities (the values of qcw_trace,
  * qcw_purity and qcw_probabilities, same arithmetic) at this point of the evolution, e.g.
  * every 100 gates as in the paper's noise studies (Sec. 5.2.3).  The paper has no asynchronous

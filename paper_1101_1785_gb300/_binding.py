@@ -57,6 +57,8 @@ SIGNATURES = {
     "qcw_trace": (I, [P, PD, PD]),
     "qcw_purity": (I, [P, PD]),
     "qcw_probabilities": (I, [P, P]),
+    "qcw_polarization": (I, [P, P]),
+    "qcw_correlation": (I, [P, I, I, P]),
     "qcw_checkpoint": (I, [P, PLL]),
     "qcw_checkpoint_read": (I, [P, LL, P]),
     "qcw_measure": (I, [P, I, I, D, PI, PD]),
@@ -303,6 +305,18 @@ class Density:
         out = np.zeros(self.n, dtype=np.float64)
         check(lib().qcw_probabilities(self.h, _p(out)), "qcw_probabilities")
         return out
+
+    def polarization(self) -> np.ndarray:
+        """Polarisation vectors Tr[sigma^(q) rho], shape (n, 3) (x, y, z per qubit)."""
+        out = np.zeros(3 * self.n, dtype=np.float64)
+        check(lib().qcw_polarization(self.h, _p(out)), "qcw_polarization")
+        return out.reshape(self.n, 3)
+
+    def correlation(self, q1: int, q2: int) -> np.ndarray:
+        """Spin correlation tensor Tr[sigma_i^(q1) sigma_j^(q2) rho], shape (3, 3)."""
+        out = np.zeros(9, dtype=np.float64)
+        check(lib().qcw_correlation(self.h, int(q1), int(q2), _p(out)), "qcw_correlation")
+        return out.reshape(3, 3)
 
     def checkpoint(self) -> int:
         """Enqueue the trace / purity / probability reductions of the current rho (flushes queued

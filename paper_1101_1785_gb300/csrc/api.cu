@@ -681,6 +681,57 @@ extern "C" qcw_status qcw_purity(qcw_ctx *ctx, double *out)
     return QCW_OK;
 }
 
+// ------------------------------------------------------------------ Pauli expectations
+// Term (qubit q, Pauli p = 1, 2, 3) added to a string's masks.
+static void pauli_add(PauliTerms &T, int s, int n, int q, int p)
+{
+    const unsigned b = 1u << (n - 1 - q);
+    if (p == 1) T.flip[s] |= b;
+    if (p == 2) T.flip[s] |= b, T.ym[s] |= b, T.ny[s]++;
+    if (p == 3) T.zm[s] |= b;
+}
+
+static qcw_status pauli_readout(qcw_ctx *c, const PauliTerms &T)
+{
+    qcw_status st = fused_flush(c);
+    if (st) return st;
+    launch_pauli_expect(c->rho, c->n, T, c->d_partials, c->red_blocks * (QCW_MAX_QUBITS + 2), c->d_result, c->stream);
+    CKLAUNCH(c, 2);
+    return fetch_results(c);
+}
+
+extern "C" qcw_status qcw_polarization(qcw_ctx *ctx, double *out)
+{
+    CHECK_CTX(ctx);
+    if (!out) return set_error(QCW_EINVAL, "null output");
+    PauliTerms T{};
+    T.count = 3 * ctx->n;
+    for (int q = 0; q < ctx->n; q++)
+        for (int i = 0; i < 3; i++) pauli_add(T, 3 * q + i, ctx->n, q, i + 1);
+    qcw_status st = pauli_readout(ctx, T);
+    if (st) return st;
+    memcpy(out, ctx->h_result, sizeof(double) * (size_t)T.count);
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_correlation(qcw_ctx *ctx, int q1, int q2, double *out)
+{
+    CHECK_CTX(ctx);
+    if (!out) return set_error(QCW_EINVAL, "null output");
+    if (q1 < 0 || q1 >= ctx->n || q2 < 0 || q2 >= ctx->n || q1 == q2) return set_error(QCW_EINVAL, "bad qubits");
+    PauliTerms T{};
+    T.count = 9;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            pauli_add(T, 3 * i + j, ctx->n, q1, i + 1);
+            pauli_add(T, 3 * i + j, ctx->n, q2, j + 1);
+        }
+    qcw_status st = pauli_readout(ctx, T);
+    if (st) return st;
+    memcpy(out, ctx->h_result, sizeof(double) * 9);
+    return QCW_OK;
+}
+
 // ------------------------------------------------------------------ asynchronous readouts
 // Slot layout: Re tr, Im tr, P(q = 1) for q < QCW_MAX_QUBITS (n used), purity at 2 + n, and the
 // context's error word in the last entry.

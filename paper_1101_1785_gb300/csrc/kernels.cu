@@ -520,6 +520,56 @@ __global__ void __launch_bounds__(RED_THREADS) k_purity_lower(const float4 *__re
     block_store<1>(acc, 1, partials);
 }
 
+// Tr[P rho] = sum_r P[r][r ^ f] rho[r ^ f][r] for a Pauli string P with flip mask f (its X and
+// Y qubits' label bits): P[r][r ^ f] = (-1)^(Z qubits set in r) i^(2 (Y qubits set in r) - #Y)
+// (sigma_y[0][1] = -i, sigma_y[1][0] = i).  rho[r ^ f][r] is read from the lower triangle
+// (conjugated when r ^ f < r), so half storage needs no completion.  One term after the other,
+// each thread sums its rows in FP64, then a fixed tree per block: partials[block][term].
+__global__ void __launch_bounds__(RED_THREADS) k_pauli_expect(const float2 *__restrict__ rho, int n,
+                                                              const __grid_constant__ PauliTerms T,
+                                                              double *__restrict__ partials)
+{
+    __shared__ double sh[RED_THREADS / 32];
+    const uint64_t dim = 1ull << n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int s = 0; s < T.count; s++) {
+        const uint64_t flip = T.flip[s], ym = T.ym[s], zm = T.zm[s];
+        const int ny = T.ny[s];
+        double acc = 0;
+        for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < dim;
+             r += (uint64_t)gridDim.x * blockDim.x) {
+            const uint64_t t = r ^ flip;
+            float2 z = t >= r ? rho[t * dim + r] : rho[r * dim + t];
+            if (t < r) z.y = -z.y;
+            const int k = (2 * __popcll(r & ym) - ny) & 3;
+            float v = k == 0 ? z.x : k == 1 ? -z.y : k == 2 ? -z.x : z.y;
+            if (__popcll(r & zm) & 1) v = -v;
+            acc += (double)v;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sh[w] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int j = 0; j < RED_THREADS / 32; j++) t += sh[j];
+            partials[(size_t)blockIdx.x * T.count + s] = t;
+        }
+        __syncthreads();
+    }
+}
+
+void launch_pauli_expect(const float2 *rho, int n, const PauliTerms &T, double *partials, int max_partials,
+                         double *out, cudaStream_t s)
+{
+    const uint64_t dim = 1ull << n;
+    const uint64_t need = (dim + RED_THREADS - 1) / RED_THREADS;
+    uint64_t nb = (uint64_t)max_partials / (uint64_t)T.count;
+    if (nb > need) nb = need;
+    if (nb < 1) nb = 1;
+    k_pauli_expect<<<(unsigned)nb, RED_THREADS, 0, s>>>(rho, n, T, partials);
+    k_fold<<<T.count, 32, 0, s>>>(partials, (int)nb, T.count, out);
+}
+
 // out[0] = the sum of nblocks partials (fixed tree).
 void launch_fold(const double *partials, int nblocks, double *out, cudaStream_t s)
 {

@@ -78,6 +78,17 @@ void launch_project(float2 *rho, int n, int qubit, int m, float scale, int nsm, 
 void launch_symmetrize(float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_purity_lower(const float2 *rho, int n, double *partials, double *out, int nblocks, cudaStream_t s);
 void launch_fold(const double *partials, int nblocks, double *out, cudaStream_t s);
+// Pauli-string expectations Tr[P rho] (polarisation vectors, spin correlation tensor): per
+// string the row-label masks of its X-or-Y qubits (flipped), Y qubits and Z qubits.
+constexpr int kMaxPauliTerms = 3 * QCW_MAX_QUBITS;
+struct PauliTerms {
+    int count;
+    unsigned flip[kMaxPauliTerms], ym[kMaxPauliTerms], zm[kMaxPauliTerms];
+    int ny[kMaxPauliTerms];
+};
+// out[s] = Re Tr[P_s rho] for s < T.count (count <= 63), reading only the lower triangle.
+void launch_pauli_expect(const float2 *rho, int n, const PauliTerms &T, double *partials, int max_partials,
+                         double *out, cudaStream_t s);
 // The purity partials of the last fused pass, if they describe the current rho.
 bool fused_purity_partials(qcw_ctx *c, const double **partials, int *nblocks);
 void launch_partial_trace(const float2 *rho, const PTParams &p, double2 *out, int nsm,

@@ -226,3 +226,40 @@ def test_determinism(q):
     a = q.run_circuit(c).get_state()
     b = q.run_circuit(c).get_state()
     np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode,kernel,n", [("plain", 0, 5), ("fused", 2, 7), ("fused", 3, 9), ("fused", 4, 10)])
+def test_polarization_and_correlation_match_oracle(q, mode, kernel, n):
+    """Polarisation vectors and spin correlation tensors (Sec. 5.2) of a noisy circuit's state,
+    on full storage (plain path, per-tile Hermitian kernel) and on the lower triangle left by
+    the warp-specialised kernels, against the oracle's traces Tr[P rho]."""
+    c = wl.random_circuit(n, 60, 5200 + n, "mixed", "adpd")
+    rho = oracle.run_circuit(c)
+    d = q.Density(n)
+    if mode == "fused":
+        d.set_mode(q.QCW_MODE_FUSED, 5)
+        d.set_fused_kernel(kernel)
+    for op in c.ops:
+        d.apply_op(op)
+    np.testing.assert_allclose(d.polarization(), oracle.polarization(rho), atol=1e-5, rtol=0)
+    for q1, q2 in ((0, n - 1), (n - 1, 1), (2, 3)):
+        np.testing.assert_allclose(d.correlation(q1, q2), oracle.correlation(rho, q1, q2), atol=1e-5, rtol=0)
+    with pytest.raises(q.QcwError) as e:
+        d.correlation(1, 1)
+    assert e.value.status == q.QCW_EINVAL
+    d.close()
+
+
+def test_bell_state_polarization_and_correlation(q):
+    """(|00> + |11>)/sqrt 2 on qubits 1 and 3 of four: the pair has no polarisation, the
+    spectators in |0> point along +z; correlation tensor diag(1, -1, 1) between the pair, zero
+    between the pair and a spectator (the product P_0 (x) P_3 = 0)."""
+    d = q.Density(4)
+    d.apply_gate1(wl.gate_matrix("H"), 1)
+    d.apply_gate2(wl.gate_matrix("CNOT"), 1, 3)
+    want = np.zeros((4, 3))
+    want[0, 2] = want[2, 2] = 1.0
+    np.testing.assert_allclose(d.polarization(), want, atol=1e-7, rtol=0)
+    np.testing.assert_allclose(d.correlation(1, 3), np.diag([1.0, -1.0, 1.0]), atol=1e-6)
+    np.testing.assert_allclose(d.correlation(0, 3), np.zeros((3, 3)), atol=1e-7)
+    d.close()
