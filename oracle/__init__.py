@@ -3,8 +3,10 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference
 legs may import this package.  The product library never loads it and shares no code
 with it.  The arithmetic lives in ``qcw_oracle.c`` (plain complex128 loops following the
-paper's pair / quartet sweeps, Sec. 3, and its Kraus form, Eq. rhoE2); this module only
-marshals numpy arrays into that library and replays circuits op by op.
+paper's pair / quartet sweeps, Sec. 3, and its Kraus form, Eq. rhoE2); this module marshals
+numpy arrays into that library and replays circuits op by op.  The spectral observables
+(entropy, fidelity) take numpy's Hermitian eigensolver as a library step on the C partial
+trace.
 """
 
 from __future__ import annotations
@@ -183,6 +185,23 @@ def polarization(rho: np.ndarray) -> np.ndarray:
 def correlation(rho: np.ndarray, q1: int, q2: int) -> np.ndarray:
     """Spin correlation tensor C_ij = Tr[sigma_i^(q1) sigma_j^(q2) rho] (Sec. 5.2), shape (3, 3)."""
     return np.array([[pauli_expectation(rho, [q1, q2], [i, j]).real for j in (1, 2, 3)] for i in (1, 2, 3)])
+
+
+def entropy(rho: np.ndarray, keep) -> float:
+    """von Neumann entropy S = -Tr[rho_A log2 rho_A] of the reduced state of `keep`, in bits
+    (Sec. 5.2: S tends to n_q in the classical limit, hence base 2)."""
+    w = np.linalg.eigvalsh(partial_trace(rho, keep))
+    w = w[w > 1e-15]
+    return float(-(w * np.log2(w)).sum())
+
+
+def fidelity(rho: np.ndarray, keep, sigma: np.ndarray) -> float:
+    """F = Tr sqrt(sqrt(sigma) rho_A sqrt(sigma)) (Sec. 5.2) of the reduced state of `keep`
+    against the caller's sigma."""
+    ra = partial_trace(rho, keep)
+    mu, v = np.linalg.eigh(np.asarray(sigma, dtype=np.complex128))
+    s = v @ np.diag(np.sqrt(np.clip(mu, 0, None))) @ v.conj().T
+    return float(np.sqrt(np.clip(np.linalg.eigvalsh(s @ ra @ s), 0, None)).sum())
 
 
 def initial_state(circuit) -> np.ndarray:

@@ -246,6 +246,7 @@ def test_classical_limit_golden():
     np.testing.assert_allclose(oracle.purity(rho), g["purity"][0], atol=1e-9)
     ent = -sum(x * np.log2(x) for x in ev)
     np.testing.assert_allclose(ent, g["entropy_bits"][0], atol=1e-8)
+    np.testing.assert_allclose(oracle.entropy(rho, list(range(n))), g["entropy_bits"][0], atol=1e-8)
     assert np.abs(rho - np.diag(np.diag(rho))).max() < 1e-9
 
 
@@ -420,3 +421,37 @@ def test_polarization_of_a_product_state():
     for q in range(3):
         np.testing.assert_allclose(pol[q], bloch(f[q]), atol=1e-14)
     np.testing.assert_allclose(oracle.correlation(rho, 0, 2), np.outer(bloch(f[0]), bloch(f[2])), atol=1e-14)
+
+
+def test_entropy_and_fidelity_of_entangled_states():
+    """Bell pair: the whole state is pure (0 bits), each qubit maximally mixed (1 bit), whose
+    fidelity with |0><0| is 1/sqrt 2 and with I/2 is 1; GHZ on five qubits: any two qubits
+    carry 1 bit; a product of pure states has 0 bits everywhere."""
+    rho = _zero(2)
+    oracle.apply_unitary(rho, wl.gate_matrix("H"), [0])
+    oracle.apply_unitary(rho, wl.gate_matrix("CNOT"), [0, 1])
+    assert abs(oracle.entropy(rho, [0, 1])) < 1e-12
+    assert abs(oracle.entropy(rho, [0]) - 1) < 1e-12 and abs(oracle.entropy(rho, [1]) - 1) < 1e-12
+    assert abs(oracle.fidelity(rho, [1], np.diag([1.0, 0.0])) - 2 ** -0.5) < 1e-12
+    assert abs(oracle.fidelity(rho, [0], np.eye(2) / 2) - 1) < 1e-12
+    ghz = _zero(5)
+    oracle.apply_unitary(ghz, wl.gate_matrix("H"), [0])
+    for q in range(1, 5):
+        oracle.apply_unitary(ghz, wl.gate_matrix("CNOT"), [0, q])
+    assert abs(oracle.entropy(ghz, [1, 3]) - 1) < 1e-12
+    prod = _zero(3)
+    oracle.apply_unitary(prod, wl.gate_matrix("H"), [1])
+    for keep in ([0], [1], [0, 2], [0, 1, 2]):
+        assert abs(oracle.entropy(prod, keep)) < 1e-12
+
+
+def test_fidelity_of_a_state_with_itself_and_commuting_states():
+    """F(rho_A, rho_A) = 1 for a mixed reduced state; diagonal (commuting) states give
+    sum_i sqrt(p_i q_i)."""
+    rng = np.random.default_rng(33)
+    rho = random_rho(rng, 4)
+    ra = oracle.partial_trace(rho, [1, 3])
+    assert abs(oracle.fidelity(rho, [1, 3], ra) - 1) < 1e-10
+    p, q = rng.dirichlet(np.ones(4)), rng.dirichlet(np.ones(4))
+    d = np.diag(p).astype(np.complex128)
+    assert abs(oracle.fidelity(d, [0, 1], np.diag(q)) - np.sum(np.sqrt(p * q))) < 1e-12
