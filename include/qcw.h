@@ -215,6 +215,20 @@ QCW_API qcw_status qcw_polarization(qcw_ctx *ctx, double *out);
  * equal or out-of-range qubits.  Flushes queued work first; synchronises. */
 QCW_API qcw_status qcw_correlation(qcw_ctx *ctx, int q1, int q2, double *out);
 
+/* von Neumann entropy S = -Tr[rho_A log2 rho_A] of the reduced state rho_A of the kept qubits
+ * (Sec. 5.2; in bits, as S tends to n_q in the classical limit), keep strictly ascending,
+ * 1 <= nkeep <= 6.  rho_A is the GPU partial trace (qcw_partial_trace), its eigenvalues come
+ * from a host Jacobi eigensolver in FP64 (eigenvalues below 1e-15 count as 0).  Flushes queued
+ * work first; synchronises. */
+QCW_API qcw_status qcw_entropy(qcw_ctx *ctx, const int *keep, int nkeep, double *out);
+
+/* Fidelity F = Tr sqrt(sqrt(sigma) rho_A sqrt(sigma)) (Sec. 5.2) of the reduced state of the kept
+ * qubits with the caller's Hermitian positive semidefinite sigma (host complex128, 2^nkeep x
+ * 2^nkeep row-major, copied during the call); 1 <= nkeep <= 6.  Same path as qcw_entropy; the
+ * paper approximates F from the eigenvalues of rho . rho_0, this computes it through the
+ * Hermitian form.  Synchronises. */
+QCW_API qcw_status qcw_fidelity(qcw_ctx *ctx, const int *keep, int nkeep, const double *sigma_c128, double *out);
+
 /* Asynchronous readout of the trace, purity and probabilities (the values of qcw_trace,
  * qcw_purity and qcw_probabilities, same arithmetic) at this point of the evolution, e.g.
  * every 100 gates as in the paper's noise studies (Sec. 5.2.3).  The paper has no asynchronous

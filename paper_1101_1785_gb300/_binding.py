@@ -59,6 +59,8 @@ SIGNATURES = {
     "qcw_probabilities": (I, [P, P]),
     "qcw_polarization": (I, [P, P]),
     "qcw_correlation": (I, [P, I, I, P]),
+    "qcw_entropy": (I, [P, P, I, PD]),
+    "qcw_fidelity": (I, [P, P, I, P, PD]),
     "qcw_checkpoint": (I, [P, PLL]),
     "qcw_checkpoint_read": (I, [P, LL, P]),
     "qcw_measure": (I, [P, I, I, D, PI, PD]),
@@ -317,6 +319,21 @@ class Density:
         out = np.zeros(9, dtype=np.float64)
         check(lib().qcw_correlation(self.h, int(q1), int(q2), _p(out)), "qcw_correlation")
         return out.reshape(3, 3)
+
+    def entropy(self, keep) -> float:
+        """von Neumann entropy (bits) of the reduced state of the kept qubits (1..6, ascending)."""
+        k = np.ascontiguousarray(keep, dtype=np.int32)
+        v = D()
+        check(lib().qcw_entropy(self.h, _p(k), len(k), ctypes.byref(v)), "qcw_entropy")
+        return v.value
+
+    def fidelity(self, keep, sigma) -> float:
+        """Tr sqrt(sqrt(sigma) rho_A sqrt(sigma)) of the reduced state of `keep` with sigma."""
+        k = np.ascontiguousarray(keep, dtype=np.int32)
+        s = np.ascontiguousarray(sigma, dtype=np.complex128)
+        v = D()
+        check(lib().qcw_fidelity(self.h, _p(k), len(k), _p(s), ctypes.byref(v)), "qcw_fidelity")
+        return v.value
 
     def checkpoint(self) -> int:
         """Enqueue the trace / purity / probability reductions of the current rho (flushes queued

@@ -6,6 +6,7 @@
 #include <mutex>
 #include <string>
 
+#include "hermitian.h"
 #include "qcw_internal.h"
 
 using namespace qcw;
@@ -729,6 +730,53 @@ extern "C" qcw_status qcw_correlation(qcw_ctx *ctx, int q1, int q2, double *out)
     qcw_status st = pauli_readout(ctx, T);
     if (st) return st;
     memcpy(out, ctx->h_result, sizeof(double) * 9);
+    return QCW_OK;
+}
+
+// ------------------------------------------------------------------ entropy and fidelity
+static const int kSpectralMaxQubits = 6;
+
+// Reduced state of `keep` on the host, made exactly Hermitian ((A + A^dagger) / 2).
+static qcw_status reduced_state(qcw_ctx *c, const int *keep, int nkeep, std::vector<c128> &ra)
+{
+    if (!keep || nkeep < 1 || nkeep > kSpectralMaxQubits) return set_error(QCW_EINVAL, "1 to 6 kept qubits");
+    const int N = 1 << nkeep;
+    ra.assign((size_t)N * N, c128(0, 0));
+    qcw_status st = qcw_partial_trace(c, keep, nkeep, reinterpret_cast<double *>(ra.data()));
+    if (st) return st;
+    for (int a = 0; a < N; a++)
+        for (int b = a; b < N; b++) {
+            const c128 h = 0.5 * (ra[(size_t)a * N + b] + std::conj(ra[(size_t)b * N + a]));
+            ra[(size_t)a * N + b] = h;
+            ra[(size_t)b * N + a] = std::conj(h);
+        }
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_entropy(qcw_ctx *ctx, const int *keep, int nkeep, double *out)
+{
+    CHECK_CTX(ctx);
+    if (!out) return set_error(QCW_EINVAL, "null output");
+    std::vector<c128> ra;
+    qcw_status st = reduced_state(ctx, keep, nkeep, ra);
+    if (st) return st;
+    const int N = 1 << nkeep;
+    std::vector<double> w(N);
+    herm_eig(ra.data(), N, w.data(), nullptr);
+    *out = entropy_bits(w.data(), N);
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_fidelity(qcw_ctx *ctx, const int *keep, int nkeep, const double *sigma_c128, double *out)
+{
+    CHECK_CTX(ctx);
+    if (!out || !sigma_c128) return set_error(QCW_EINVAL, "null argument");
+    std::vector<c128> ra;
+    qcw_status st = reduced_state(ctx, keep, nkeep, ra);
+    if (st) return st;
+    const int N = 1 << nkeep;
+    std::vector<c128> sigma(reinterpret_cast<const c128 *>(sigma_c128), reinterpret_cast<const c128 *>(sigma_c128) + (size_t)N * N);
+    *out = fidelity_root(ra.data(), sigma.data(), N);
     return QCW_OK;
 }
 

@@ -263,3 +263,39 @@ def test_bell_state_polarization_and_correlation(q):
     np.testing.assert_allclose(d.correlation(1, 3), np.diag([1.0, -1.0, 1.0]), atol=1e-6)
     np.testing.assert_allclose(d.correlation(0, 3), np.zeros((3, 3)), atol=1e-7)
     d.close()
+
+
+@pytest.mark.parametrize("mode,kernel,n", [("plain", 0, 6), ("fused", 3, 9), ("fused", 4, 8)])
+def test_entropy_and_fidelity_match_oracle(q, mode, kernel, n):
+    """Subsystem entropy and fidelity (Sec. 5.2) of a noisy circuit's state: GPU partial trace,
+    host eigensolver, against the oracle's reduced states and numpy's eigensolver."""
+    c = wl.random_circuit(n, 60, 5300 + n, "mixed", "adpd")
+    rho = oracle.run_circuit(c)
+    rng = np.random.default_rng(n)
+    d = q.Density(n)
+    if mode == "fused":
+        d.set_mode(q.QCW_MODE_FUSED, 5)
+        d.set_fused_kernel(kernel)
+    for op in c.ops:
+        d.apply_op(op)
+    for keep in ([0], [1, n - 1], [0, 2, 3]):
+        assert abs(d.entropy(keep) - oracle.entropy(rho, keep)) <= 1e-5
+        sigma = random_rho(rng, len(keep))
+        assert abs(d.fidelity(keep, sigma) - oracle.fidelity(rho, keep, sigma)) <= 1e-5
+    for bad in ([], list(range(7)), [2, 1]):
+        with pytest.raises(q.QcwError) as e:
+            d.entropy(bad)
+        assert e.value.status == q.QCW_EINVAL
+    d.close()
+
+
+def test_entropy_of_a_bell_pair(q):
+    """(|00> + |11>)/sqrt 2 on qubits 0 and 2 of three: each qubit of the pair 1 bit, the pair
+    and the spectator 0 bits, fidelity of qubit 0 with |0><0| 1/sqrt 2."""
+    d = q.Density(3)
+    d.apply_gate1(wl.gate_matrix("H"), 0)
+    d.apply_gate2(wl.gate_matrix("CNOT"), 0, 2)
+    assert abs(d.entropy([0]) - 1) < 1e-6 and abs(d.entropy([2]) - 1) < 1e-6
+    assert abs(d.entropy([0, 2])) < 1e-6 and abs(d.entropy([1])) < 1e-6
+    assert abs(d.fidelity([0], np.diag([1.0, 0.0])) - 2 ** -0.5) < 1e-6
+    d.close()
