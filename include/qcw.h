@@ -160,8 +160,11 @@ QCW_API qcw_status qcw_apply_gate2(qcw_ctx *ctx, const double u[32], int q1, int
 QCW_API qcw_status qcw_apply_gate(qcw_ctx *ctx, const double *u, const int *qubits, int k);
 
 /* rho <- sum_j K_j rho K_j^dagger (the Kraus / POVM form of the paper's ensemble average,
- * Sec. 5.2.2, Eq. rhoE2) for nkraus (1..16) operators of k (1 or 2) qubits, stored one after
- * another (nkraus * 2 * 4^k doubles).  Trace-decreasing sets are accepted as given. */
+ * Sec. 5.2.2, Eq. rhoE2) for nkraus (1..16) operators of k (1..QCW_MAX_GATE_QUBITS) qubits,
+ * stored one after another (nkraus * 2 * 4^k doubles).  Trace-decreasing sets are accepted as
+ * given.  One- and two-qubit channels act as composed superoperators (and join fused passes);
+ * wider ones run term by term on the plain path with two scratch copies of rho, allocated on
+ * first use and kept until the context is destroyed. */
 QCW_API qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkraus, const int *qubits,
                            int k);
 

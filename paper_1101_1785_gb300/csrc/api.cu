@@ -156,7 +156,7 @@ qcw_status plain_gate2(qcw_ctx *c, const c128 *u, int q1, int q2, const int *ctr
 }
 
 // k-qubit dense gate as two passes: U on the row labels, then conj(U) on the column labels.
-qcw_status plain_gatek(qcw_ctx *c, const c128 *u, const int *qs, int k)
+qcw_status plain_gatek(qcw_ctx *c, const c128 *u, const int *qs, int k, float2 *target = nullptr)
 {
     const int n = c->n, m = 1 << k;
     for (int side = 0; side < 2; side++) {
@@ -176,7 +176,7 @@ qcw_status plain_gatek(qcw_ctx *c, const c128 *u, const int *qs, int k)
             for (int b = a + 1; b < k; b++)
                 if (v[b] < v[a]) { int t = v[a]; v[a] = v[b]; v[b] = t; }
         for (int j = 0; j < k; j++) p.pos[j] = v[j];
-        launch_gatek_side(p, c->rho, n, c->nsm, c->stream);
+        launch_gatek_side(p, target ? target : c->rho, n, c->nsm, c->stream);
         CKLAUNCH(c, 1);
     }
     return QCW_OK;
@@ -215,11 +215,38 @@ qcw_status ensure_full(qcw_ctx *c)
     return QCW_OK;
 }
 
+// Kraus channel on k >= 3 qubits (Eq. rhoE2 term by term): acc = sum_j K_j rho K_j^dagger, each
+// term on a copy of rho with the dense k-qubit side passes (K_j on the rows, conj(K_j) on the
+// columns), then rho = acc.  Two scratch copies of rho stay allocated for later channels.
+static qcw_status plain_kraus_list(qcw_ctx *c, const QOp &op)
+{
+    const size_t bytes = sizeof(float2) << (2 * c->n);
+    for (float2 **b : {&c->d_kacc, &c->d_ktmp})
+        if (!*b && cudaMalloc(b, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *b = nullptr;
+            return set_error(QCW_ENOMEM, "Kraus scratch");
+        }
+    const size_t msz = (size_t)1 << (2 * op.k);
+    const size_t nk = op.m.size() / msz;
+    CK(cudaMemsetAsync(c->d_kacc, 0, bytes, c->stream));
+    for (size_t j = 0; j < nk; j++) {
+        CK(cudaMemcpyAsync(c->d_ktmp, c->rho, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        qcw_status st = plain_gatek(c, op.m.data() + j * msz, op.qubits, op.k, c->d_ktmp);
+        if (st) return st;
+        launch_accumulate(c->d_kacc, c->d_ktmp, c->n, c->nsm, c->stream);
+        CKLAUNCH(c, 1);
+    }
+    CK(cudaMemcpyAsync(c->rho, c->d_kacc, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return QCW_OK;
+}
+
 qcw_status plain_apply(qcw_ctx *c, const QOp &op)
 {
     c->state_ver++;
     qcw_status fs = ensure_full(c);
     if (fs) return fs;
+    if (op.kind == 2) return plain_kraus_list(c, op);
     if (op.kind == 1) return plain_super(c, op.m, op.qubits, op.k);
     if (op.k == 1) return plain_gate1(c, op.m.data(), op.qubits[0], op.controls, op.ncontrols);
     if (op.k == 2) return plain_gate2(c, op.m.data(), op.qubits[0], op.qubits[1], op.controls, op.ncontrols);
@@ -248,6 +275,8 @@ static void ctx_free(qcw_ctx *c)
     if (c->d_result) cudaFree(c->d_result);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->d_staging) cudaFree(c->d_staging);
+    if (c->d_kacc) cudaFree(c->d_kacc);
+    if (c->d_ktmp) cudaFree(c->d_ktmp);
     if (c->d_ckpt) cudaFree(c->d_ckpt);
     if (c->h_ckpt) cudaFreeHost(c->h_ckpt);
     for (cudaEvent_t e : c->ckpt_ev)
@@ -532,18 +561,18 @@ extern "C" qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkr
 {
     CHECK_CTX(ctx);
     if (!kraus) return set_error(QCW_EINVAL, "null Kraus set");
-    if (k < 1 || k > 2) return set_error(QCW_EINVAL, "channels act on 1 or 2 qubits");
+    if (k < 1 || k > QCW_MAX_GATE_QUBITS) return set_error(QCW_EINVAL, "channels act on 1 to 5 qubits");
     if (nkraus < 1 || nkraus > 16) return set_error(QCW_EINVAL, "nkraus out of range");
     qcw_status st = check_qubits(ctx->n, qubits, k, nullptr, 0);
     if (st) return st;
     size_t cnt = (size_t)nkraus << (2 * k);
     if (!all_finite(kraus, 2 * cnt)) return set_error(QCW_EINVAL, "non-finite matrix entry");
     QOp op;
-    op.kind = 1;
+    op.kind = k <= 2 ? 1 : 2;
     op.k = k;
     for (int j = 0; j < k; j++) op.qubits[j] = qubits[j];
     op.ncontrols = 0;
-    op.m = kraus_superop(to_c128(kraus, cnt), nkraus, k);
+    op.m = k <= 2 ? kraus_superop(to_c128(kraus, cnt), nkraus, k) : to_c128(kraus, cnt);
     return submit(ctx, std::move(op));
 }
 

@@ -338,6 +338,23 @@ void launch_gatek_side(const GateKParams &p, float2 *rho, int n, int nsm, cudaSt
     }
 }
 
+// acc += x, element-wise (Kraus sums over more than two qubits).
+__global__ void k_accumulate(float4 *__restrict__ acc, const float4 *__restrict__ x, uint64_t n4)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n4;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const float4 a = acc[t], b = x[t];
+        acc[t] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+    }
+}
+
+void launch_accumulate(float2 *acc, const float2 *x, int n, int nsm, cudaStream_t s)
+{
+    const uint64_t n4 = (1ull << (2 * n)) / 2;
+    k_accumulate<<<grid_for(n4, 256, nsm), 256, 0, s>>>(reinterpret_cast<float4 *>(acc),
+                                                        reinterpret_cast<const float4 *>(x), n4);
+}
+
 // --------------------------------------------------------------------- state set-up
 __global__ void k_zero_state(float4 *__restrict__ rho4, uint64_t n4)
 {

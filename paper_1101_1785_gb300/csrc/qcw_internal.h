@@ -78,6 +78,7 @@ void launch_project(float2 *rho, int n, int qubit, int m, float scale, int nsm, 
 void launch_symmetrize(float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_purity_lower(const float2 *rho, int n, double *partials, double *out, int nblocks, cudaStream_t s);
 void launch_fold(const double *partials, int nblocks, double *out, cudaStream_t s);
+void launch_accumulate(float2 *acc, const float2 *x, int n, int nsm, cudaStream_t s);
 // Pauli-string expectations Tr[P rho] (polarisation vectors, spin correlation tensor): per
 // string the row-label masks of its X-or-Y qubits (flipped), Y qubits and Z qubits.
 constexpr int kMaxPauliTerms = 3 * QCW_MAX_QUBITS;
@@ -97,12 +98,13 @@ int launches_per_reduce();
 
 // ------------------------------------------------------------------ queued operation
 struct QOp {
-    int kind;               // 0 = unitary, 1 = superoperator (channel)
+    int kind;               // 0 = unitary, 1 = superoperator (channel), 2 = Kraus list (k >= 3)
     int k;                  // number of qubits (1..5)
     int qubits[5];
     int ncontrols;
     int controls[QCW_MAX_QUBITS];
-    std::vector<c128> m;    // unitary 2^k x 2^k, or superoperator 4^k x 4^k
+    std::vector<c128> m;    // unitary 2^k x 2^k, superoperator 4^k x 4^k, or the Kraus operators
+                            // (2^k x 2^k each) one after another
 };
 
 struct FusedPlan;  // planner.cpp
@@ -142,6 +144,9 @@ struct qcw_ctx {
     // Version of rho: bumped by everything that changes it.  The last fused pass of a flush
     // also sums |rho_rc|^2 over what it writes (per-CTA partials in the fused runtime);
     // purity_ver records the version those partials describe.
+    // scratch copies of rho for Kraus channels on more than two qubits (allocated on first use)
+    float2 *d_kacc = nullptr;
+    float2 *d_ktmp = nullptr;
     unsigned long long state_ver = 1;
     unsigned long long purity_ver = 0;
     // asynchronous readouts: QCW_CHECKPOINT_SLOTS slots of kCkptVals doubles on the device and

@@ -299,3 +299,35 @@ def test_entropy_of_a_bell_pair(q):
     assert abs(d.entropy([0, 2])) < 1e-6 and abs(d.entropy([1])) < 1e-6
     assert abs(d.fidelity([0], np.diag([1.0, 0.0])) - 2 ** -0.5) < 1e-6
     d.close()
+
+
+@pytest.mark.parametrize("mode,k", [("plain", 3), ("fused", 3), ("plain", 4)])
+def test_kraus_channels_on_three_and_four_qubits(q, mode, k):
+    """A random trace-preserving channel on k = 3, 4 qubits (three Kraus operators cut from a
+    Haar isometry, Eq. rhoE2) between two noisy circuit halves, against the oracle; in fused
+    mode the wide channel splits the queue and runs on the plain path."""
+    n = 6
+    rng = np.random.default_rng(40 + k)
+    d_k = 1 << k
+    iso = haar_unitary(rng, 3 * d_k)[:, :d_k]
+    ks = np.stack([iso[d_k * j:d_k * (j + 1)] for j in range(3)])
+    qubits = [int(x) for x in rng.permutation(n)[:k]]
+    c = wl.random_circuit(n, 20, 4400 + k, "mixed", "adpd")
+    rho0 = random_rho(rng, n)
+    want = rho0.copy()
+    d = q.Density(n)
+    if mode == "fused":
+        d.set_mode(q.QCW_MODE_FUSED, 4)
+    d.set_state(rho0)
+    for op in c.ops:
+        d.apply_op(op)
+        oracle.apply_op(want, op)
+    d.apply_kraus(ks, qubits)
+    oracle.apply_kraus(want, ks, qubits)
+    for op in c.ops:
+        d.apply_op(op)
+        oracle.apply_op(want, op)
+    got = d.get_state()
+    assert np.abs(got - want).max() <= 1e-5
+    assert abs(d.trace() - oracle.trace(want)) <= 1e-6
+    d.close()
