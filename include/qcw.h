@@ -168,6 +168,37 @@ QCW_API qcw_status qcw_apply_gate(qcw_ctx *ctx, const double *u, const int *qubi
 QCW_API qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkraus, const int *qubits,
                            int k);
 
+/* ---------------------------------------------------------------- multiverse ensemble */
+
+/* The paper's own noise method (Sec. 5.2.1, Eq. rhoE1; notebooks MV1 / MV2 / MVn): an ensemble
+ * of nvec state vectors ("universes"), each evolved by the one- and two-qubit operators of
+ * Sec. 3 (Op1 / Op2: Eqs. resmat1, resmat2), each noise step applying one operator Omega_k per
+ * vector, chosen by the caller (the random draws of the method are the caller's), and the
+ * density matrix formed as rho = sum_v w_v |psi_v><psi_v|.  With every branch of every noise
+ * step enumerated and sqrt(p_k) folded into the Omega_k, the result equals the Kraus-sum
+ * evolution (Eq. rhoE2).  Vectors are complex64 on the device, label bit n - 1 - q for qubit q;
+ * operations are asynchronous on the ensemble's own stream. */
+typedef struct qcw_ensemble qcw_ensemble;
+/* nvec (1..65536) vectors of nqubits (1..QCW_MAX_QUBITS), all |0..0>. */
+QCW_API qcw_status qcw_ensemble_create(int nqubits, int nvec, qcw_ensemble **out);
+QCW_API qcw_status qcw_ensemble_destroy(qcw_ensemble *e);
+/* Load / read all vectors: nvec * 2 * 2^n doubles (complex128, vector after vector). */
+QCW_API qcw_status qcw_ensemble_set(qcw_ensemble *e, const double *psi_c128);
+QCW_API qcw_status qcw_ensemble_get(qcw_ensemble *e, double *psi_c128);
+/* psi_v <- U psi_v for every vector: U 2 x 2 on `target` (Eq. resmat1) or 4 x 4 on (q1, q2) with
+ * the quartet order 2 q(q1) + q(q2) (Eq. resmat2); row-major complex128. */
+QCW_API qcw_status qcw_ensemble_apply_gate1(qcw_ensemble *e, const double u[8], int target);
+QCW_API qcw_status qcw_ensemble_apply_gate2(qcw_ensemble *e, const double u[32], int q1, int q2);
+/* Noise step on `target`: psi_v <- Omega_{choice[v]} psi_v, Omega_0..Omega_{nomega-1} (1..16
+ * one-qubit operators, 2 x 2 complex128 each, one after another); choice (host, nvec ints in
+ * 0..nomega-1) holds the caller's draws.  QCW_EINVAL on a choice out of range. */
+QCW_API qcw_status qcw_ensemble_apply_noise1(qcw_ensemble *e, const double *omegas, int nomega, int target,
+                                          const int *choice);
+/* ctx's rho <- sum_v weights[v] |psi_v><psi_v| (weights: host, nvec doubles; FP32 sums of FP32
+ * products).  ctx must have the ensemble's qubit count; its queued work is dropped as by
+ * qcw_set_state.  Ordered after the ensemble's operations; asynchronous on ctx's stream. */
+QCW_API qcw_status qcw_ensemble_density(qcw_ensemble *e, const double *weights, qcw_ctx *ctx);
+
 /* One element of a circuit handed over in a single call (qcw_apply_ops). */
 #define QCW_OP_GATE 0
 #define QCW_OP_KRAUS 1

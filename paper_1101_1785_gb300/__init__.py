@@ -16,6 +16,7 @@ from ._binding import (  # noqa: F401
     SIGNATURES,
     Batch,
     Density,
+    Ensemble,
     Server,
     QcwResult,
     PackedOps,

@@ -61,6 +61,14 @@ SIGNATURES = {
     "qcw_correlation": (I, [P, I, I, P]),
     "qcw_entropy": (I, [P, P, I, PD]),
     "qcw_fidelity": (I, [P, P, I, P, PD]),
+    "qcw_ensemble_create": (I, [I, I, PP]),
+    "qcw_ensemble_destroy": (I, [P]),
+    "qcw_ensemble_set": (I, [P, P]),
+    "qcw_ensemble_get": (I, [P, P]),
+    "qcw_ensemble_apply_gate1": (I, [P, P, I]),
+    "qcw_ensemble_apply_gate2": (I, [P, P, I, I]),
+    "qcw_ensemble_apply_noise1": (I, [P, P, I, I, P]),
+    "qcw_ensemble_density": (I, [P, P, P]),
     "qcw_checkpoint": (I, [P, PLL]),
     "qcw_checkpoint_read": (I, [P, LL, P]),
     "qcw_measure": (I, [P, I, I, D, PI, PD]),
@@ -169,6 +177,53 @@ def _ints(xs) -> np.ndarray:
 
 def _p(a: np.ndarray):
     return a.ctypes.data_as(P) if a is not None and a.size else None
+
+
+class Ensemble:
+    """Multiverse ensemble: nvec device state vectors of n qubits (qcw_ensemble_*)."""
+
+    def __init__(self, n: int, nvec: int):
+        h = P()
+        check(lib().qcw_ensemble_create(int(n), int(nvec), ctypes.byref(h)), "qcw_ensemble_create")
+        self.h, self.n, self.nvec = h, int(n), int(nvec)
+
+    def set(self, psi):
+        a = np.ascontiguousarray(psi, dtype=np.complex128).reshape(self.nvec, 1 << self.n)
+        check(lib().qcw_ensemble_set(self.h, _p(a)), "qcw_ensemble_set")
+
+    def get(self) -> np.ndarray:
+        out = np.zeros((self.nvec, 1 << self.n), dtype=np.complex128)
+        check(lib().qcw_ensemble_get(self.h, _p(out)), "qcw_ensemble_get")
+        return out
+
+    def apply_gate1(self, u, target: int):
+        a = np.ascontiguousarray(u, dtype=np.complex128)
+        check(lib().qcw_ensemble_apply_gate1(self.h, _p(a), int(target)), "qcw_ensemble_apply_gate1")
+
+    def apply_gate2(self, u, q1: int, q2: int):
+        a = np.ascontiguousarray(u, dtype=np.complex128)
+        check(lib().qcw_ensemble_apply_gate2(self.h, _p(a), int(q1), int(q2)), "qcw_ensemble_apply_gate2")
+
+    def apply_noise1(self, omegas, target: int, choice):
+        om = np.ascontiguousarray(omegas, dtype=np.complex128)
+        ch = np.ascontiguousarray(choice, dtype=np.int32)
+        check(lib().qcw_ensemble_apply_noise1(self.h, _p(om), om.shape[0], int(target), _p(ch)),
+              "qcw_ensemble_apply_noise1")
+
+    def density(self, weights, d: "Density"):
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        check(lib().qcw_ensemble_density(self.h, _p(w), d.h), "qcw_ensemble_density")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().qcw_ensemble_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Density:

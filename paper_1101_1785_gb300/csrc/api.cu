@@ -416,6 +416,14 @@ extern "C" qcw_status qcw_set_fused_wait_limit(qcw_ctx *ctx, unsigned polls, int
     return QCW_OK;
 }
 
+qcw_status qcw::begin_state_replace(qcw_ctx *c)
+{
+    c->queue.clear();
+    c->half = false;
+    c->state_ver++;
+    return clear_error_word(c);
+}
+
 extern "C" qcw_status qcw_reset(qcw_ctx *ctx)
 {
     CHECK_CTX(ctx);

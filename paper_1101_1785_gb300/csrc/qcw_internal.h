@@ -178,6 +178,9 @@ void fused_destroy(qcw_ctx *ctx);
 void fused_collect_timing(qcw_ctx *ctx);
 qcw_status plain_apply(qcw_ctx *c, const QOp &op);
 qcw_status ensure_full(qcw_ctx *c);
+// rho is about to be overwritten from outside the queue: drop queued work, mark the storage
+// full, bump the state version and clear the error word.
+qcw_status begin_state_replace(qcw_ctx *c);
 // Validate an op list against an n-qubit register and convert it to queued operations
 // (Kraus sets become superoperators); nothing is appended on error.
 qcw_status convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out);

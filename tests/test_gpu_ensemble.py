@@ -1,0 +1,115 @@
+"""GPU parity of the multiverse ensemble (Sec. 5.2.1, Eq. rhoE1) against the oracle: the
+ensemble's state vectors follow the oracle's Op1 / Op2 sweeps, and an ensemble that enumerates
+every branch of its noise steps reproduces the Kraus-sum evolution of the density matrix
+(Eq. rhoE2)."""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests._helpers import haar_unitary
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1101_1785_gb300 as q
+
+    return q
+
+
+def _random_vectors(rng, nvec, n):
+    psi = rng.normal(size=(nvec, 1 << n)) + 1j * rng.normal(size=(nvec, 1 << n))
+    return psi / np.linalg.norm(psi, axis=1, keepdims=True)
+
+
+def test_ensemble_gates_match_oracle_statevectors(q):
+    n, nvec = 5, 7
+    rng = np.random.default_rng(61)
+    psi = _random_vectors(rng, nvec, n)
+    e = q.Ensemble(n, nvec)
+    e.set(psi)
+    want = psi.copy()
+    for step in range(30):
+        if step % 3 == 2:
+            a, b = [int(x) for x in rng.permutation(n)[:2]]
+            u = haar_unitary(rng, 4)
+            e.apply_gate2(u, a, b)
+            for v in range(nvec):
+                oracle.apply_vec(want[v], u, [a, b])
+        else:
+            t = int(rng.integers(n))
+            u = haar_unitary(rng, 2)
+            e.apply_gate1(u, t)
+            for v in range(nvec):
+                oracle.apply_vec(want[v], u, [t])
+    assert np.abs(e.get() - want).max() <= 1e-5
+    e.close()
+
+
+def test_enumerated_multiverse_equals_kraus_sum(q):
+    """Two noise steps of Eq. rhoE1's form (Omega = sqrt(p) I, sqrt((1 - p)/3) X, Y, Z) between
+    gates: 16 universes, one per branch pair, weight 1 each (the sqrt(p_k) sit in the
+    operators).  Their density matrix equals the oracle's Kraus evolution, and so do its trace,
+    purity and polarisation readouts."""
+    n, p = 3, 0.9
+    rng = np.random.default_rng(62)
+    xyz = [wl.gate_matrix(s) for s in ("X", "Y", "Z")]
+    omegas = np.stack([np.sqrt(p) * np.eye(2)] + [np.sqrt((1 - p) / 3) * m for m in xyz])
+    gates = [("u1", haar_unitary(rng, 2), (0,)), ("noise", None, (1,)), ("u2", wl.gate_matrix("CNOT"), (0, 1)),
+             ("u1", haar_unitary(rng, 2), (2,)), ("noise", None, (0,)), ("u2", haar_unitary(rng, 4), (2, 1))]
+    psi0 = _random_vectors(rng, 1, n)[0]
+    branches = list(itertools.product(range(4), repeat=2))
+    e = q.Ensemble(n, len(branches))
+    e.set(np.tile(psi0, (len(branches), 1)))
+    rho = np.outer(psi0, psi0.conj())
+    step = 0
+    for kind, u, qs in gates:
+        if kind == "u1":
+            e.apply_gate1(u, qs[0])
+            oracle.apply_unitary(rho, u, list(qs))
+        elif kind == "u2":
+            e.apply_gate2(u, qs[0], qs[1])
+            oracle.apply_unitary(rho, u, list(qs))
+        else:
+            e.apply_noise1(omegas, qs[0], [b[step] for b in branches])
+            oracle.apply_kraus(rho, omegas, list(qs))
+            step += 1
+    d = q.Density(n)
+    e.density(np.ones(len(branches)), d)
+    assert np.abs(d.get_state() - rho).max() <= 1e-5
+    assert abs(d.trace() - oracle.trace(rho)) <= 1e-6
+    assert abs(d.purity() - oracle.purity(rho)) <= 1e-5
+    np.testing.assert_allclose(d.polarization(), oracle.polarization(rho), atol=1e-5, rtol=0)
+    d.close()
+    e.close()
+
+
+def test_density_weights_and_validation(q):
+    """One-hot weights give |psi_v><psi_v|; a noise choice out of range and a qubit-count
+    mismatch are rejected."""
+    n, nvec = 4, 3
+    rng = np.random.default_rng(63)
+    psi = _random_vectors(rng, nvec, n)
+    e = q.Ensemble(n, nvec)
+    e.set(psi)
+    d = q.Density(n)
+    e.density([0.0, 1.0, 0.0], d)
+    assert np.abs(d.get_state() - np.outer(psi[1], psi[1].conj())).max() <= 1e-6
+    with pytest.raises(q.QcwError) as err:
+        e.apply_noise1(np.stack([np.eye(2)]), 0, [0, 1, 0])
+    assert err.value.status == q.QCW_EINVAL
+    d3 = q.Density(3)
+    with pytest.raises(q.QcwError) as err:
+        e.density(np.ones(nvec), d3)
+    assert err.value.status == q.QCW_EINVAL
+    d.close()
+    d3.close()
+    e.close()
