@@ -4,6 +4,8 @@
 #include "qcw_device.cuh"
 #include "qcw_internal.h"
 
+#include <cmath>
+#include <utility>
 #include <vector>
 
 struct qcw_ensemble {
