@@ -374,3 +374,34 @@ def test_best_search_packs_no_more_passes_than_order(shim):
     _, best = _plan(shim, n, 4, ops, 1)
     assert len(best) <= len(order)
     assert len(best) < 0.9 * len(order)
+
+
+def test_trace_row_of_two_qubit_transfer_matrices(shim):
+    """Trace-preserving operations (unitaries, channels cut from isometries) give two-qubit
+    transfer matrices whose row 0 -- the trace component in the Pauli basis -- is (1/4, 0, ..., 0)
+    up to rounding residue, so the tensor-core phases, which round R to TF32 pieces, leave the
+    trace exact (0.25 and 0 are TF32 numbers)."""
+    rng = np.random.default_rng(71)
+    n = 5
+    ops = []
+    for _ in range(80):
+        r = rng.random()
+        if r < 0.3:
+            ops.append(("u", (int(rng.integers(n)),), haar_unitary(rng, 2)))
+        elif r < 0.6:
+            a, b = [int(x) for x in rng.permutation(n)[:2]]
+            ops.append(("u", (a, b), haar_unitary(rng, 4)))
+        elif r < 0.85:
+            iso = haar_unitary(rng, 6)[:, :2]
+            ops.append(("k", (int(rng.integers(n)),), [iso[2 * j:2 * j + 2] for j in range(3)]))
+        else:
+            a, b = [int(x) for x in rng.permutation(n)[:2]]
+            iso = haar_unitary(rng, 8)[:, :4]
+            ops.append(("k", (a, b), [iso[4 * j:4 * j + 4] for j in range(2)]))
+    phases, cf = _tile_plan(shim, n, 4, True, 12, ops)
+    two = [off for kind, _, off, _, _ in phases if kind == 2]
+    assert len(two) >= 10
+    for off in two:
+        row0 = np.array([cf[off + 8 * f].real for f in range(16)])
+        assert abs(row0[0] - 0.25) < 1e-12
+        assert np.abs(row0[1:]).max() < 1e-12
