@@ -10,6 +10,14 @@ in FP64; at the end it reads the per-qubit probabilities, measures qubit 0 (u-dr
 projective measurement with renormalisation) and takes the partial trace over qubits 0, 1.
 
 Metric: gate-applications/s = gates per step x steps (x GPUs) / time.  One JSON line.
+
+Beside the timed steps (untimed for the headline, each with its own numbers in the line): an
+accuracy replay of one step against the complex128 oracle's stored readouts of the full
+circuit; the oracle itself timed on a warm sample on every host core and on one; and, at one
+GPU, three sub-measurements -- the 12-qubit depolarising circuit on the plain path (one launch
+per gate and per channel, GB/s per launch), the 512-circuit batch in one persistent launch
+against the one-circuit-at-a-time loop, and 5 s of the Poisson request stream through the
+continuous-batching server (p50 / p99 latency, req/s) against the same loop.
 ``--impl reference`` times the CPU oracle on a bounded sample of the same workload.
 """
 
@@ -36,6 +44,8 @@ CHUNK = 100
 FUSE_K = 0  # 0: the library's cost model picks the width per segment
 U_MEASURE = 0.37
 PT_KEEP = [0, 1]
+GOLDEN_N14 = os.path.join(ROOT, "tests", "golden", "config3_n14.txt")
+GOLDEN_N12 = os.path.join(ROOT, "tests", "golden", "config2_n12.txt")
 
 
 def parse_args():
@@ -45,10 +55,13 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="qcw", choices=["qcw", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-gates", type=int, default=1, help="gates of the oracle sample")
-    ap.add_argument("--workload", default="circuit14", choices=["circuit14", "batch", "serve"],
-                    help="circuit14: the 14-qubit benchmark (default); batch: 512 circuits of 4..10 qubits in "
-                         "one launch; serve: Poisson request stream through the continuous-batching server")
+    ap.add_argument("--cpu-gates", type=int, default=3, help="gates of the timed oracle sample (all cores)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the untimed accuracy leg and the plain / batch / serve sub-measurements")
+    ap.add_argument("--workload", default="circuit14", choices=["circuit14", "plain12", "batch", "serve"],
+                    help="circuit14: the 14-qubit benchmark (default); plain12: the 12-qubit depolarising circuit "
+                         "on the plain path, one launch per gate and per channel; batch: 512 circuits of 4..10 "
+                         "qubits in one launch; serve: Poisson request stream through the continuous-batching server")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "herm", "herm_ws", "herm_tc"],
@@ -208,19 +221,50 @@ def recorded_traffic(kernel):
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_sample(ngates: int):
-    """Oracle on the first `ngates` gates (+ channels) of the same circuit; returns (gates/s, s, threads)."""
+def oracle_timed(ngates: int, steps: int = 1, warmup: int = 0, one_core: bool = False):
+    """The oracle as it stands on bounded, warm samples of the benchmark circuit.  The first gate
+    (with its AD + PD channels) runs untimed on every core to touch the state's pages; then each
+    of `warmup` + `steps` samples runs the next `ngates` gates on every core (the first `warmup`
+    untimed), and with one_core the gate after those runs on one thread.  Returns (seconds per
+    timed sample, threads used, one-thread seconds or None)."""
     import oracle
     import workloads as wl
 
-    c = wl.config3_circuit(n=N_QUBITS, ngates=N_GATES).gate_prefix(ngates)
-    threads = oracle.set_threads(0)
+    c = wl.config3_circuit(n=N_QUBITS, ngates=N_GATES)
+    nthreads = os.cpu_count() or 1
+    used = oracle.set_threads(nthreads)
+    bounds = [len(c.gate_prefix(g).ops) for g in range(0, N_GATES + 1)]
     rho = oracle.initial_state(c)
-    t0 = time.perf_counter()
-    oracle.run_circuit(c, rho)
-    dt = time.perf_counter() - t0
+    oracle.run_circuit(c, rho, c.ops[:bounds[1]])
+    g = 1
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        oracle.run_circuit(c, rho, c.ops[bounds[g]:bounds[g + ngates]])
+        dt = time.perf_counter() - t0
+        g += ngates
+        if i >= warmup:
+            times.append(dt)
+    one = None
+    if one_core:
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.run_circuit(c, rho, c.ops[bounds[g]:bounds[g + 1]])
+        one = time.perf_counter() - t0
+        oracle.set_threads(nthreads)
     del rho
-    return ngates / dt, dt, threads
+    return times, used, one
+
+
+def cpu_baseline_legs(ngates: int):
+    """Every core on `ngates` warm gates, then one core on the next gate."""
+    times, used, one = oracle_timed(ngates, 1, 0, one_core=True)
+    dt = times[0]
+    sample = (f"gates 2..{ngates + 1} of the 1000-gate 14-qubit circuit with their AD+PD channels on the complex128 "
+              f"oracle, {used} host threads, after one untimed warm-up gate ({dt:.1f} s); then gate {ngates + 2} on "
+              f"one thread ({one:.1f} s)")
+    return {"value": ngates / dt, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+            "one_core": {"value": 1.0 / one, "unit": UNIT, "cores": 1, "seconds": one}}
 
 
 def run_reference(args):
@@ -229,18 +273,14 @@ def run_reference(args):
         return
     import workloads  # noqa: F401
 
-    for _ in range(args.warmup):
-        oracle_sample(args.cpu_gates)
+    ngates = max(1, args.cpu_gates)
     t0 = time.perf_counter()
-    total = 0.0
-    threads = 0
-    for _ in range(args.steps):
-        _, dt, threads = oracle_sample(args.cpu_gates)
-        total += dt
+    times, threads, _ = oracle_timed(ngates, args.steps, args.warmup)
     elapsed = time.perf_counter() - t0
-    value = args.cpu_gates * args.steps / total
-    sample = (f"first {args.cpu_gates} gate(s) of the 1000-gate 14-qubit circuit with their AD+PD "
-              f"channels, complex128 oracle, per step")
+    total = sum(times)
+    value = ngates * args.steps / total
+    sample = (f"{ngates} consecutive gates of the 1000-gate 14-qubit circuit with their AD+PD channels per step "
+              f"(from gate 2 on, after one untimed warm-up gate), complex128 oracle on {threads} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -252,6 +292,86 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": elapsed,
     }), flush=True)
+
+
+# ----------------------------------------------------------------------------- accuracy
+def read_golden(path):
+    """Stored oracle readouts (tests/golden/make_deep_goldens.py): 'key values...' lines."""
+    import numpy as np
+
+    g = {"elem": [], "ckpt": [], "ptrace": {}, "post_ptrace": {}}
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            if key == "elem":
+                g["elem"].append([float(x) for x in vals])
+            elif key == "ckpt":
+                g["ckpt"].append([float(x) for x in vals])
+            elif key in ("ptrace", "post_ptrace"):
+                z = np.array([float(x) for x in vals[2:]])
+                g[key][(int(vals[0]), int(vals[1]))] = (z[0::2] + 1j * z[1::2]).reshape(4, 4)
+            else:
+                g[key] = [float(x) for x in vals]
+    return g
+
+
+def sampled_element_error(d, elem):
+    """max |delta rho| over stored (row, column, Re, Im) elements, gathered on the device from the
+    context's buffer (completed and ordered on its stream)."""
+    import numpy as np
+    import torch
+
+    ptr, sp = d.device_state()
+    torch.cuda.ExternalStream(sp).synchronize()
+    dim = 1 << d.n
+
+    class _Buf:
+        pass
+
+    buf = _Buf()
+    buf.__cuda_array_interface__ = {"shape": (dim, 2 * dim), "typestr": "<f4", "data": (ptr, False), "version": 2}
+    view = torch.as_tensor(buf, device="cuda")
+    e = np.asarray(elem, dtype=np.float64)
+    r = torch.as_tensor(e[:, 0].astype(np.int64), device="cuda")
+    c2 = torch.as_tensor(2 * e[:, 1].astype(np.int64), device="cuda")
+    got = view[r, c2].double().cpu().numpy() + 1j * view[r, c2 + 1].double().cpu().numpy()
+    return float(np.abs(got - (e[:, 2] + 1j * e[:, 3])).max())
+
+
+def accuracy_n14(d, packed):
+    """Untimed replay of one step on the timed context, every readout against the complex128
+    oracle's values for the full 1000-gate circuit."""
+    import numpy as np
+
+    if not os.path.exists(GOLDEN_N14):
+        return {"vs": None, "why": "no stored oracle readouts for the 14-qubit circuit"}
+    g = read_golden(GOLDEN_N14)
+    d.reset()
+    tickets = []
+    for p in packed:
+        d.apply_packed(p)
+        tickets.append(d.checkpoint())
+    ck = [d.checkpoint_read(t) for t in tickets]
+    out = {
+        "vs": "complex128 oracle, full circuit (tests/golden/config3_n14.txt)",
+        "checkpoints": len(ck),
+        "max_abs_trace_err": max(abs(c[0] - 1) for c in ck),
+        "max_abs_dtrace": max(abs(c[0].real - w[1]) for c, w in zip(ck, g["ckpt"])),
+        "max_abs_dpurity": max(abs(c[1] - w[3]) for c, w in zip(ck, g["ckpt"])),
+        "max_abs_dp": max(float(np.abs(c[2] - np.asarray(w[4:])).max()) for c, w in zip(ck, g["ckpt"])),
+    }
+    out["max_abs_drho_sampled"] = sampled_element_error(d, g["elem"])
+    out["sampled_elements"] = len(g["elem"])
+    out["max_abs_drho_A"] = max(float(np.abs(d.partial_trace(list(k)) - v).max()) for k, v in g["ptrace"].items())
+    m, pm = d.measure(0, -1, U_MEASURE)
+    out["outcome_match"] = int(m) == int(g["measure"][2])
+    out["abs_dp_outcome"] = abs(pm - g["measure"][3])
+    out["post_max_abs_drho_A"] = float(np.abs(d.partial_trace([0, 1]) - g["post_ptrace"][(0, 1)]).max())
+    out["post_abs_dpurity"] = abs(d.purity() - g["post_purity"][0])
+    return out
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -342,6 +462,9 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+    accuracy = None
+    if rank == 0 and not args.no_extras and nq == N_QUBITS:
+        accuracy = accuracy_n14(d, packed)
     d.close()
 
     total_gates = N_GATES * args.steps * world
@@ -356,10 +479,14 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and nq == N_QUBITS:
-        v, dt, threads = oracle_sample(args.cpu_gates)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {args.cpu_gates} gate(s) of the same circuit with their AD+PD channels "
-                         f"on the complex128 oracle ({dt:.1f} s)"}
+        cpu = cpu_baseline_legs(args.cpu_gates)
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        import paper_1101_1785_gb300 as q2
+
+        extras["plain12"] = measure_plain12(q2, steps=2, warmup=1)
+        extras["batch"] = measure_batch(q2, steps=3, warmup=3)
+        extras["serve"] = measure_serve(q2, rate=2000.0, duration=5.0)
 
     if rank == 0:
         line = {
@@ -386,8 +513,9 @@ def run_ours(args):
             "fused_passes_per_step": st["fused_passes"] / args.steps,
             "clocks": clocks,
             "checks": {"max_abs_trace_err": max_tr_err, "final_purity": tp[-1][1],
-                       "outcome_q0": meas[0], "p_outcome": meas[1]},
+                       "outcome_q0": meas[0], "p_outcome": meas[1], "accuracy_vs_oracle": accuracy},
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -419,15 +547,74 @@ def _loop_one_at_a_time(q, circuits, packed, reps=1):
     return dt, out
 
 
-def run_batch(args):
+def measure_plain12(q, steps=2, warmup=1):
+    """The 12-qubit depolarising circuit on the plain path: one kernel launch per gate and per
+    channel (500 gates, one Kraus channel per touched qubit).  rho_0 is uploaded before each step,
+    outside the timed region; the step ends with the trace, purity and probabilities.  Each launch
+    reads and writes rho once: 16 * 4^12 algorithmic bytes."""
     import numpy as np
     import torch
 
-    import __graft_entry__
     import workloads as wl
 
-    __graft_entry__.build()
-    import paper_1101_1785_gb300 as q
+    c = wl.config2_circuit()
+    n = c.n
+    bounds = [len(c.gate_prefix(g).ops) for g in range(0, c.n_gates + 1, CHUNK)]
+    packed = [q.PackedOps(c.ops[bounds[i]:bounds[i + 1]]) for i in range(len(bounds) - 1)]
+    rho0 = np.ascontiguousarray(c.rho0.astype(np.complex64))
+    host = torch.from_numpy(rho0.view(np.float32).reshape(-1)).pin_memory()
+    d = q.Density(n)
+    _, sp = d.device_state()
+    stream = torch.cuda.ExternalStream(sp)
+    ms_total, readouts = 0.0, None
+    d.stats_reset()
+    for i in range(warmup + steps):
+        d.set_state_c64(host.data_ptr())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if i == warmup:
+            d.stats_reset()
+        e0.record(stream)
+        for p in packed:
+            d.apply_packed(p)
+        tr, pu, pr = d.trace(), d.purity(), d.probabilities()
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            ms_total += e0.elapsed_time(e1)
+        readouts = (tr, pu, pr)
+    st = d.stats()
+    peaks, peak_kind = load_peaks()
+    launches = len(c.ops)
+    ms = ms_total / steps
+    gbs = launches * 16 * 4 ** n / (ms / 1e3) / 1e9
+    out = {
+        "workload": "12-qubit density matrix, rho0 = I/2^n/2 + |psi><psi|/2, 500 gates (70 % Haar SU(2), 30 % "
+                    "CNOT/CZ), depolarising 1e-3 per touched qubit; plain path, one launch per gate and per channel",
+        "gate_apps_per_s": c.n_gates / (ms / 1e3), "ms_per_step": ms, "steps": steps,
+        "evolution_launches_per_step": launches, "gpu_launches_per_step": st["launches"] / steps,
+        "bytes_per_launch": 16 * 4 ** n, "achieved_gbs": gbs, "frac_of_hbm": gbs / float(peaks["hbm_gbs"]),
+        "peak_kind": peak_kind, "l2_bytes": torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size,
+        "rho_bytes": 8 * 4 ** n,
+    }
+    if os.path.exists(GOLDEN_N12):
+        g = read_golden(GOLDEN_N12)
+        tr, pu, pr = readouts
+        out["accuracy_vs_oracle"] = {
+            "vs": "complex128 oracle, full circuit (tests/golden/config2_n12.txt)",
+            "abs_trace_err": abs(tr - 1), "abs_dpurity": abs(pu - g["final"][2]),
+            "max_abs_dp": float(np.abs(pr - np.asarray(g["final"][3:])).max()),
+            "max_abs_drho_sampled": sampled_element_error(d, g["elem"]), "sampled_elements": len(g["elem"]),
+            "max_abs_drho_A": max(float(np.abs(d.partial_trace(list(k)) - v).max()) for k, v in g["ptrace"].items()),
+        }
+    d.close()
+    return out
+
+
+def measure_batch(q, steps=3, warmup=3):
+    import numpy as np
+    import torch
+
+    import workloads as wl
 
     torch.cuda.init()
     circuits = wl.config4_batch()
@@ -435,52 +622,47 @@ def run_batch(args):
     t0 = time.perf_counter()
     b = q.Batch(circuits)
     t_create = time.perf_counter() - t0
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         b.run()
         b.wait()
     sampler = ClockSampler(0)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         b.run()
         b.wait()
-    dt = (time.perf_counter() - t0) / args.steps
+    dt = (time.perf_counter() - t0) / steps
     clocks = sampler.stop()
-    _, pur, _ = b.results()
+    _, pur, tr = b.results()
     info = b.info()
     b.close()
     packed = [q.PackedOps(c.ops) for c in circuits]
     _loop_one_at_a_time(q, circuits[:16], packed[:16])  # warm-up
     dt_loop, pur_loop = _loop_one_at_a_time(q, circuits, packed)
-    print(json.dumps({
+    return {
         "metric": "gate-applications/s, 512-circuit batch (n ~ U{4..10}, depth ~ U{50..400}, AD+PD)",
-        "value": gates / dt, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
-        "ms_per_step": dt * 1e3, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
-        "config": {"workload": "512 seeded circuits, one persistent graph-captured launch", "circuits": len(circuits),
-                   "gates": gates},
+        "value": gates / dt, "unit": UNIT, "steps": steps, "warmup": max(3, warmup),
+        "ms_per_step": dt * 1e3, "circuits": len(circuits), "gates": gates,
         "circuits_per_s": len(circuits) / dt,
         "plain_loop": {"value": gates / dt_loop, "ms_per_batch": dt_loop * 1e3,
                        "circuits_per_s": len(circuits) / dt_loop},
         "speedup_vs_plain_loop": dt_loop / dt,
         "max_abs_purity_diff_vs_plain": float(np.abs(pur - pur_loop).max()),
+        "failed_1e-5_check": int(np.sum((np.abs(pur - pur_loop) > 1e-5) | (np.abs(tr - 1) > 1e-5))),
         "plan": info, "create_s": t_create, "clocks": clocks,
-    }), flush=True)
+    }
 
 
-def run_serve(args):
+def measure_serve(q, rate=2000.0, duration=10.0):
     import threading
 
     import numpy as np
     import torch
 
-    import __graft_entry__
     import workloads as wl
 
-    __graft_entry__.build()
-    import paper_1101_1785_gb300 as q
-
     torch.cuda.init()
-    reqs = wl.config5_requests(rate=args.rate, duration=args.duration)
-    warm = wl.config5_requests(rate=args.rate, duration=0.2, index=1)
+    reqs = wl.config5_requests(rate=rate, duration=duration)
+    warm = wl.config5_requests(rate=rate, duration=0.2, index=1)
     packed = [q.PackedOps(c.ops) for _, c in reqs]
     wpacked = [q.PackedOps(c.ops) for _, c in warm]
     srv = q.Server(48 << 30, max_live=8192, passes_per_step=4)
@@ -509,7 +691,7 @@ def run_serve(args):
     while not (done_sub.is_set() and len(results) == len(reqs)):
         srv.step()
         results += srv.poll()
-        if not results and time.monotonic() - start > args.duration + 600:
+        if not results and time.monotonic() - start > duration + 600:
             break
     th.join()
     clocks = sampler.stop()
@@ -520,29 +702,49 @@ def run_serve(args):
     gates = sum(c.n_gates for _, c in reqs)
     sample = min(len(reqs), 2000)
     dt_loop, _ = _loop_one_at_a_time(q, [c for _, c in reqs[:sample]], packed[:sample])
-    print(json.dumps({
+    return {
         "metric": "req/s and p99 latency, Poisson request stream (n 3..13, depth 20..500, mixed noise)",
-        "value": len(results) / (t_end - start), "unit": "req/s", "n_gpus": 1, "higher_is_better": True,
-        "dtype": "c64", "data": "synthetic",
-        "config": {"workload": f"Poisson {args.rate:g} req/s for {args.duration:g} s, budget 48 GiB (16*4^n per "
+        "value": len(results) / (t_end - start), "unit": "req/s",
+        "config": {"workload": f"Poisson {rate:g} req/s for {duration:g} s, budget 48 GiB (16*4^n per "
                                f"request), 4 passes per engine step", "requests": len(reqs)},
         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                        "max": float(lat.max() * 1e3)},
-        "gate_apps_per_s": gates / (t_end - start), "offered_req_per_s": args.rate,
-        "bad_results": bad,
+        "gate_apps_per_s": gates / (t_end - start), "offered_req_per_s": rate,
+        "failed_1e-5_check": bad,
         "plain_loop": {"req_per_s": sample / dt_loop, "sample": sample},
         "clocks": clocks,
-    }), flush=True)
+    }
+
+
+def _standalone(args, what):
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import torch
+
+    import paper_1101_1785_gb300 as q
+
+    torch.cuda.set_device(0)
+    if what == "plain12":
+        r = measure_plain12(q, steps=args.steps, warmup=max(1, args.warmup))
+        r.update({"metric": "gate-applications/s, 12-qubit plain path (GB/s per launch vs peak)", "value":
+                  r["gate_apps_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "c64",
+                  "data": "synthetic"})
+    elif what == "batch":
+        r = measure_batch(q, steps=args.steps, warmup=args.warmup)
+        r.update({"n_gpus": 1, "higher_is_better": True, "dtype": "c64", "data": "synthetic"})
+    else:
+        r = measure_serve(q, rate=args.rate, duration=args.duration)
+        r.update({"n_gpus": 1, "higher_is_better": True, "dtype": "c64", "data": "synthetic"})
+    print(json.dumps(r), flush=True)
 
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batch":
-        run_batch(args)
-    elif args.workload == "serve":
-        run_serve(args)
+    elif args.workload in ("plain12", "batch", "serve"):
+        _standalone(args, args.workload)
     else:
         run_ours(args)
 

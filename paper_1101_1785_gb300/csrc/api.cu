@@ -827,21 +827,28 @@ extern "C" qcw_status qcw_checkpoint(qcw_ctx *ctx, long long *ticket)
     CHECK_CTX(ctx);
     if (!ticket) return set_error(QCW_EINVAL, "null ticket");
     if (!ctx->d_ckpt) {
+        // All or nothing: the ring is published into the context only once every piece exists,
+        // so a failure here leaves the context as it was (the next call tries again).
         const size_t bytes = sizeof(double) * QCW_CHECKPOINT_SLOTS * kCkptVals;
-        if (cudaMalloc(&ctx->d_ckpt, bytes) != cudaSuccess) {
+        double *dbuf = nullptr, *hbuf = nullptr;
+        cudaEvent_t ev[QCW_CHECKPOINT_SLOTS] = {};
+        bool ok = cudaMalloc(&dbuf, bytes) == cudaSuccess && cudaMallocHost(&hbuf, bytes) == cudaSuccess;
+        for (int i = 0; ok && i < QCW_CHECKPOINT_SLOTS; i++)
+            ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
-            ctx->d_ckpt = nullptr;
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+            if (hbuf) cudaFreeHost(hbuf);
+            if (dbuf) cudaFree(dbuf);
             return set_error(QCW_ENOMEM, "checkpoint slots");
-        }
-        if (cudaMallocHost(&ctx->h_ckpt, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            ctx->h_ckpt = nullptr;
-            return set_error(QCW_ENOMEM, "pinned checkpoint slots");
         }
         for (int i = 0; i < QCW_CHECKPOINT_SLOTS; i++) {
             ctx->ckpt_ticket[i] = -1;
-            CK(cudaEventCreateWithFlags(&ctx->ckpt_ev[i], cudaEventDisableTiming));
+            ctx->ckpt_ev[i] = ev[i];
         }
+        ctx->h_ckpt = hbuf;
+        ctx->d_ckpt = dbuf;
     }
     qcw_status st = fused_flush(ctx);
     if (st) return st;

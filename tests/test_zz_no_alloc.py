@@ -52,6 +52,22 @@ def test_static_partial_trace_matches_allocating_one(q):
         d.close()
 
 
+def test_static_partial_trace_block_reduction_and_empty_keep(q):
+    """Tracing out eight or more qubits takes the block-reduction kernel; keeping none returns
+    the 1 x 1 matrix holding the trace.  The two calls run back to back on the same array."""
+    rng = np.random.default_rng(2027)
+    d = q.Density(12)
+    d.set_state(random_rho(rng, 12))
+    want = d.partial_trace([0, 5])
+    got = _static_ptrace(q, d, [0, 5])  # 10 qubits traced out
+    assert np.abs(got - want).max() <= TOL
+    tr = _static_ptrace(q, d, [])
+    assert tr.shape == (1, 1)
+    assert abs(tr[0, 0] - d.trace()) <= TOL
+    assert abs(tr[0, 0] - np.trace(want)) <= TOL
+    d.close()
+
+
 def test_static_partial_trace_rejects_large_outputs(q):
     d = q.Density(8)
     with pytest.raises(q.QcwError) as e:
