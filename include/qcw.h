@@ -61,6 +61,9 @@ typedef enum {
 #define QCW_MAX_QUBITS 17
 /* Largest k accepted by qcw_apply_gate. */
 #define QCW_MAX_GATE_QUBITS 5
+/* Most Kraus operators in one channel: the paper's multiverse noise step (Eq. rhoE4) has
+ * 1 + 2 n_p of them for n_p paths with one- and two-hit noise operators. */
+#define QCW_MAX_KRAUS 64
 
 /* --------------------------------------------------------------------- lifetime */
 
@@ -160,7 +163,7 @@ QCW_API qcw_status qcw_apply_gate2(qcw_ctx *ctx, const double u[32], int q1, int
 QCW_API qcw_status qcw_apply_gate(qcw_ctx *ctx, const double *u, const int *qubits, int k);
 
 /* rho <- sum_j K_j rho K_j^dagger (the Kraus / POVM form of the paper's ensemble average,
- * Sec. 5.2.2, Eq. rhoE2) for nkraus (1..16) operators of k (1..QCW_MAX_GATE_QUBITS) qubits,
+ * Sec. 5.2.2, Eq. rhoE2) for nkraus (1..QCW_MAX_KRAUS) operators of k (1..QCW_MAX_GATE_QUBITS) qubits,
  * stored one after another (nkraus * 2 * 4^k doubles).  Trace-decreasing sets are accepted as
  * given.  One- and two-qubit channels act as composed superoperators (and join fused passes);
  * wider ones run term by term on the plain path with two scratch copies of rho, allocated on
@@ -206,7 +209,7 @@ typedef struct {
     int kind;           /* QCW_OP_GATE or QCW_OP_KRAUS */
     int k;              /* qubits: 1..QCW_MAX_GATE_QUBITS for a gate, 1..2 for Kraus */
     int qubits[QCW_MAX_GATE_QUBITS]; /* first k entries used, paper order */
-    int nkraus;         /* Kraus operators (1..16) for QCW_OP_KRAUS; ignored for gates */
+    int nkraus;         /* Kraus operators (1..QCW_MAX_KRAUS) for QCW_OP_KRAUS; ignored for gates */
     long long offset;   /* index, in doubles, of the op's first matrix in `matrices` */
 } qcw_op;
 
@@ -255,6 +258,13 @@ QCW_API qcw_status qcw_correlation(qcw_ctx *ctx, int q1, int q2, double *out);
  * from a host Jacobi eigensolver in FP64 (eigenvalues below 1e-15 count as 0).  Flushes queued
  * work first; synchronises. */
 QCW_API qcw_status qcw_entropy(qcw_ctx *ctx, const int *keep, int nkeep, double *out);
+
+/* Eigenvalues of the reduced state rho_A of the kept qubits, ascending, into out[2^nkeep]
+ * (Sec. 5.2.3: the eigenvalues are monitored as the noise drives rho to the classical form,
+ * where they all approach 1 / 2^n_q).  keep strictly ascending, 1 <= nkeep <= 6; the GPU
+ * partial trace followed by the host Jacobi eigensolver in FP64, as qcw_entropy.  Flushes
+ * queued work first; synchronises. */
+QCW_API qcw_status qcw_eigenvalues(qcw_ctx *ctx, const int *keep, int nkeep, double *out);
 
 /* Fidelity F = Tr sqrt(sqrt(sigma) rho_A sqrt(sigma)) (Sec. 5.2) of the reduced state of the kept
  * qubits with the caller's Hermitian positive semidefinite sigma (host complex128, 2^nkeep x

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqcw.so")
 QCW_OK, QCW_EINVAL, QCW_ENOMEM, QCW_ECUDA, QCW_EZEROPROB, QCW_ETIMEOUT, QCW_ENOTSUP = range(7)
 QCW_MODE_PLAIN, QCW_MODE_FUSED = 0, 1
 QCW_MAX_QUBITS = 17
+QCW_MAX_KRAUS = 64
 
 _lock = threading.Lock()
 _lib = None
@@ -60,6 +61,7 @@ SIGNATURES = {
     "qcw_polarization": (I, [P, P]),
     "qcw_correlation": (I, [P, I, I, P]),
     "qcw_entropy": (I, [P, P, I, PD]),
+    "qcw_eigenvalues": (I, [P, P, I, P]),
     "qcw_fidelity": (I, [P, P, I, P, PD]),
     "qcw_ensemble_create": (I, [I, I, PP]),
     "qcw_ensemble_destroy": (I, [P]),
@@ -381,6 +383,13 @@ class Density:
         v = D()
         check(lib().qcw_entropy(self.h, _p(k), len(k), ctypes.byref(v)), "qcw_entropy")
         return v.value
+
+    def eigenvalues(self, keep) -> np.ndarray:
+        """Eigenvalues (ascending) of the reduced state of the kept qubits."""
+        k = _ints(sorted(keep))
+        out = np.zeros(1 << len(k), dtype=np.float64)
+        check(lib().qcw_eigenvalues(self.h, _p(k), len(k), _p(out)), "qcw_eigenvalues")
+        return out
 
     def fidelity(self, keep, sigma) -> float:
         """Tr sqrt(sqrt(sigma) rho_A sqrt(sigma)) of the reduced state of `keep` with sigma."""

@@ -8,6 +8,7 @@
 
 #include "hermitian.h"
 #include "qcw_internal.h"
+#include "tile.h"
 
 using namespace qcw;
 
@@ -110,9 +111,16 @@ static std::vector<c128> kraus_superop(const std::vector<c128> &ks, int nk, int 
 // ------------------------------------------------------------------ plain launches
 namespace qcw {
 
+qcw_status plain_super(qcw_ctx *c, const std::vector<c128> &s, const int *qs, int k);
+static std::vector<c128> gate_superop(const c128 *u, int k);
+
+// An uncontrolled gate runs as its superoperator U (x) conj U in the Pauli basis (k_super1 /
+// k_super2), which keeps the trace exactly where the complex product would let the rounding of
+// U's entries move it; controlled gates act on the row and the column side separately.
 qcw_status plain_gate1(qcw_ctx *c, const c128 *u, int t, const int *ctrl, int nc)
 {
     const int n = c->n;
+    if (nc == 0) return plain_super(c, gate_superop(u, 1), &t, 1);
     Gate1Params p{};
     for (int i = 0; i < 4; i++) p.u[i] = f2(u[i]);
     p.pc = n - 1 - t;
@@ -143,6 +151,10 @@ static void quartet_layout(int n, int q1, int q2, int *pos, uint64_t *offr, uint
 qcw_status plain_gate2(qcw_ctx *c, const c128 *u, int q1, int q2, const int *ctrl, int nc)
 {
     const int n = c->n;
+    if (nc == 0) {
+        const int qs[2] = {q1, q2};
+        return plain_super(c, gate_superop(u, 2), qs, 2);
+    }
     Gate2Params p{};
     for (int i = 0; i < 16; i++) p.u[i] = f2(u[i]);
     quartet_layout(n, q1, q2, p.pos, p.off_r, p.off_c);
@@ -182,18 +194,35 @@ qcw_status plain_gatek(qcw_ctx *c, const c128 *u, const int *qs, int k, float2 *
     return QCW_OK;
 }
 
+// Superoperator of a k-qubit gate: S = U (x) conj(U), index (row, column) of the group member.
+static std::vector<c128> gate_superop(const c128 *u, int k)
+{
+    const int d = 1 << k, D = d * d;
+    std::vector<c128> s((size_t)D * D);
+    for (int r2 = 0; r2 < d; r2++)
+        for (int c2 = 0; c2 < d; c2++)
+            for (int r = 0; r < d; r++)
+                for (int cc = 0; cc < d; cc++)
+                    s[(size_t)(r2 * d + c2) * D + (r * d + cc)] = u[r2 * d + r] * std::conj(u[c2 * d + cc]);
+    return s;
+}
+
 qcw_status plain_super(qcw_ctx *c, const std::vector<c128> &s, const int *qs, int k)
 {
     const int n = c->n;
     if (k == 1) {
         Super1Params p{};
-        for (int i = 0; i < 16; i++) p.s[i] = f2(s[i]);
+        double R[4][4];
+        pauli_transfer1(s.data(), R);
+        for (int i = 0; i < 16; i++) p.r[i] = (float)R[i / 4][i % 4];
         p.pc = n - 1 - qs[0];
         p.pr = 2 * n - 1 - qs[0];
         launch_super1(p, c->rho, n, c->nsm, c->stream);
     } else if (k == 2) {
         Super2Params p{};
-        for (int i = 0; i < 256; i++) p.s[i] = f2(s[i]);
+        double R[16][16];
+        pauli_transfer(s, R);
+        for (int i = 0; i < 256; i++) p.r[i] = (float)R[i / 16][i % 16];
         quartet_layout(n, qs[0], qs[1], p.pos, p.off_r, p.off_c);
         launch_super2(p, c->rho, n, c->nsm, c->stream);
     } else {
@@ -570,7 +599,7 @@ extern "C" qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkr
     CHECK_CTX(ctx);
     if (!kraus) return set_error(QCW_EINVAL, "null Kraus set");
     if (k < 1 || k > QCW_MAX_GATE_QUBITS) return set_error(QCW_EINVAL, "channels act on 1 to 5 qubits");
-    if (nkraus < 1 || nkraus > 16) return set_error(QCW_EINVAL, "nkraus out of range");
+    if (nkraus < 1 || nkraus > QCW_MAX_KRAUS) return set_error(QCW_EINVAL, "nkraus out of range");
     qcw_status st = check_qubits(ctx->n, qubits, k, nullptr, 0);
     if (st) return st;
     size_t cnt = (size_t)nkraus << (2 * k);
@@ -598,7 +627,7 @@ qcw_status qcw::convert_ops(int n, const qcw_op *ops, int nops, const double *ma
                 return set_error(QCW_EINVAL, "non-finite matrix entry");
         } else if (o.kind == QCW_OP_KRAUS) {
             if (o.k < 1 || o.k > 2) return set_error(QCW_EINVAL, "channels act on 1 or 2 qubits");
-            if (o.nkraus < 1 || o.nkraus > 16) return set_error(QCW_EINVAL, "nkraus out of range");
+            if (o.nkraus < 1 || o.nkraus > QCW_MAX_KRAUS) return set_error(QCW_EINVAL, "nkraus out of range");
             qcw_status st = check_qubits(n, o.qubits, o.k, nullptr, 0);
             if (st) return st;
             if (!all_finite(matrices + o.offset, ((size_t)2 * o.nkraus) << (2 * o.k)))
@@ -801,6 +830,17 @@ extern "C" qcw_status qcw_entropy(qcw_ctx *ctx, const int *keep, int nkeep, doub
     std::vector<double> w(N);
     herm_eig(ra.data(), N, w.data(), nullptr);
     *out = entropy_bits(w.data(), N);
+    return QCW_OK;
+}
+
+extern "C" qcw_status qcw_eigenvalues(qcw_ctx *ctx, const int *keep, int nkeep, double *out)
+{
+    CHECK_CTX(ctx);
+    if (!out) return set_error(QCW_EINVAL, "null output");
+    std::vector<c128> ra;
+    qcw_status st = reduced_state(ctx, keep, nkeep, ra);
+    if (st) return st;
+    herm_eig(ra.data(), 1 << nkeep, out, nullptr);
     return QCW_OK;
 }
 

@@ -201,6 +201,39 @@ void launch_gate2(const Gate2Params &p, float2 *rho, int n, int nsm, cudaStream_
     }
 }
 
+// Pauli-basis butterflies on one qubit of a 16-member group (members (b00, b01, b10, b11) at
+// O, O + S2, O + S1, O + S1 + S2 become (b00 + b11, b01 + b10, b01 - b10, b00 - b11)); applied
+// twice they give 2x the input.
+template <int S1, int S2, int O>
+__device__ __forceinline__ void pquad(float2 (&x)[16])
+{
+    const float2 a = x[O], b = x[O + S2], c = x[O + S1], d = x[O + S1 + S2];
+    x[O] = make_float2(a.x + d.x, a.y + d.y);
+    x[O + S2] = make_float2(b.x + c.x, b.y + c.y);
+    x[O + S1] = make_float2(b.x - c.x, b.y - c.y);
+    x[O + S1 + S2] = make_float2(a.x - d.x, a.y - d.y);
+}
+
+// Both qubits of the group: qubit 1 on member bits (3, 1), qubit 2 on (2, 0).
+__device__ __forceinline__ void pbutterflies(float2 (&x)[16])
+{
+    pquad<8, 2, 0>(x), pquad<8, 2, 1>(x), pquad<8, 2, 4>(x), pquad<8, 2, 5>(x);
+    pquad<4, 1, 0>(x), pquad<4, 1, 2>(x), pquad<4, 1, 8>(x), pquad<4, 1, 10>(x);
+}
+
+// Member index with an odd number of D components (bit pattern (row, col) = (0, 1) on a qubit).
+__host__ __device__ constexpr bool podd(int e)
+{
+    return (((e >> 3) & 1) && !((e >> 1) & 1)) != (((e >> 2) & 1) && !(e & 1));
+}
+
+// Two-qubit superoperator on a 16-member group (Eq. rhoE2 as S = sum_k K (x) conj K), applied in
+// the Pauli basis of the two qubits: butterflies, v = the coefficients (times i where odd),
+// c = R v with the real transfer matrix R, -i back where odd, butterflies again.  For a
+// trace-preserving S the first row of R is exactly (1/4, 0, ..., 0): the trace then changes
+// only by the rounding of the butterflies, with either sign, not by the rounding of S's
+// entries, whose sign is the same at every application (a drift that grows with the number of
+// channels).  Half the multiply-adds of the complex 16 x 16 product as well.
 template <int V>
 __global__ void k_super2(float2 *__restrict__ rho, uint64_t nitems, Super2Params p)
 {
@@ -211,15 +244,32 @@ __global__ void k_super2(float2 *__restrict__ rho, uint64_t nitems, Super2Params
         load16<V>(rho, g, p.off_r, p.off_c, x);
         float2 y[V][16];
 #pragma unroll
+        for (int v = 0; v < V; v++) {
+            pbutterflies(x[v]);
+#pragma unroll
+            for (int f = 0; f < 16; f++)
+                if (podd(f)) x[v][f] = make_float2(-x[v][f].y, x[v][f].x);
+        }
+#pragma unroll
         for (int e = 0; e < 16; e++) {
 #pragma unroll
             for (int v = 0; v < V; v++) y[v][e] = make_float2(0, 0);
 #pragma unroll
             for (int f = 0; f < 16; f++) {
-                float2 c = p.s[16 * e + f];
+                const float c = p.r[16 * e + f];
 #pragma unroll
-                for (int v = 0; v < V; v++) cfma(y[v][e], c, x[v][f]);
+                for (int v = 0; v < V; v++) {
+                    y[v][e].x = fmaf(c, x[v][f].x, y[v][e].x);
+                    y[v][e].y = fmaf(c, x[v][f].y, y[v][e].y);
+                }
             }
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+#pragma unroll
+            for (int e = 0; e < 16; e++)
+                if (podd(e)) y[v][e] = make_float2(y[v][e].y, -y[v][e].x);
+            pbutterflies(y[v]);
         }
         store16<V>(rho, g, p.off_r, p.off_c, y);
     }
@@ -237,18 +287,33 @@ void launch_super2(const Super2Params &p, float2 *rho, int n, int nsm, cudaStrea
 }
 
 // --------------------------------------------------------------------- one-qubit channel
-// Superoperator S = sum_k K (x) conj(K) on the quartet (x00, x01, x10, x11), e = 2*row+col.
+// Superoperator S = sum_k K (x) conj(K) (Eq. rhoE2; a gate is S = U (x) conj U) on the quartet
+// (x00, x01, x10, x11), e = 2*row+col, in the Pauli basis of the qubit: (I, X, D, Z) =
+// (x00 + x11, x01 + x10, x01 - x10, x00 - x11), v = (I, X, i D, Z), c = R v with the real
+// transfer matrix R, (c_I, c_X, -i c_D, c_Z) through the same butterflies gives S x.  A
+// trace-preserving S has the first row of R exactly (1/2, 0, 0, 0), so the trace sees only the
+// butterflies' rounding (either sign), not the fixed-sign rounding of S's entries.
 __device__ __forceinline__ void super1_quartet(const Super1Params &p, float2 (&x)[4])
 {
-    float2 y[4];
+    const float2 v[4] = {make_float2(x[0].x + x[3].x, x[0].y + x[3].y),
+                         make_float2(x[1].x + x[2].x, x[1].y + x[2].y),
+                         make_float2(x[2].y - x[1].y, x[1].x - x[2].x),  // i (x01 - x10)
+                         make_float2(x[0].x - x[3].x, x[0].y - x[3].y)};
+    float2 c[4];
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-        y[e] = make_float2(0, 0);
+        c[e] = make_float2(0, 0);
 #pragma unroll
-        for (int f = 0; f < 4; f++) cfma(y[e], p.s[4 * e + f], x[f]);
+        for (int f = 0; f < 4; f++) {
+            c[e].x = fmaf(p.r[4 * e + f], v[f].x, c[e].x);
+            c[e].y = fmaf(p.r[4 * e + f], v[f].y, c[e].y);
+        }
     }
-#pragma unroll
-    for (int e = 0; e < 4; e++) x[e] = y[e];
+    const float2 d = make_float2(c[2].y, -c[2].x);  // -i c_D
+    x[0] = make_float2(c[0].x + c[3].x, c[0].y + c[3].y);
+    x[1] = make_float2(c[1].x + d.x, c[1].y + d.y);
+    x[2] = make_float2(c[1].x - d.x, c[1].y - d.y);
+    x[3] = make_float2(c[0].x - c[3].x, c[0].y - c[3].y);
 }
 
 __global__ void k_super1_lsb(float2 *__restrict__ rho, uint64_t nq, Super1Params p)

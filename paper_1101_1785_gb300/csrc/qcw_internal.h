@@ -34,12 +34,13 @@ struct Gate2Params {
 };
 
 struct Super1Params {
-    float2 s[16];      // 4x4 superoperator, local index e = 2*row_bit + col_bit
+    float r[16];       // real 4x4 transfer matrix in the qubit's Pauli basis (pauli_transfer1)
     int pc, pr;
 };
 
 struct Super2Params {
-    float2 s[256];     // 16x16 superoperator, local index e = 4*row_local + col_local
+    float r[256];      // real 16x16 transfer matrix in the two qubits' Pauli basis (pauli_transfer),
+                       // member index e = 4*row_local + col_local = 8 r1 + 4 r2 + 2 c1 + c2
     int pos[4];
     uint64_t off_r[4], off_c[4];
 };

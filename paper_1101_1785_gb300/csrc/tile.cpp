@@ -52,6 +52,11 @@ static int tile_pos(const FPass &fp, int vbit)
 // (b00, b01, b10, b11) = (I + Z, X + D, X - D, I - Z); I, X, Z and i D are 2x the Pauli
 // coefficients tr(P b) of the 2x2 block.  Member e = 8 r_a + 4 r_b + 2 c_a + c_b keeps its bit
 // positions: Pauli index bits (2 r + c) per qubit.
+// Transfer-matrix entries below this are FP64 rounding residue of exact zeros (the entries of
+// a map of unit-norm operators are O(1)); they are stored as 0 so that, for instance, the trace
+// row of a trace-preserving map is exactly (2^-k, 0, ...).
+constexpr double kTransferZero = 1e-14;
+
 static void pauli_fwd(c128 *x)
 {
     for (int e2 = 0; e2 < 2; e2++)
@@ -93,7 +98,7 @@ static bool pauli_odd(int e) { return (((e >> 3) & 1) && !((e >> 1) & 1)) != (((
 // inv(fwd(x)) = 4 x, R = (1/16) d fwd(S inv(.)) conj(d) with d = i on odd indices.  R is real
 // because S preserves Hermiticity (every gate and channel does): in the Hermitian Pauli basis
 // its matrix is real, and the d factors turn D into the Y coefficient.
-static void pauli_transfer(const std::vector<c128> &S, double R[16][16])
+void pauli_transfer(const std::vector<c128> &S, double R[16][16])
 {
     c128 M[16][16];
     for (int f = 0; f < 16; f++) {
@@ -114,7 +119,7 @@ static void pauli_transfer(const std::vector<c128> &S, double R[16][16])
             c128 z = M[e][f] / 16.0;
             if (pauli_odd(e)) z *= c128(0, 1);
             if (pauli_odd(f)) z *= c128(0, -1);
-            R[e][f] = z.real();
+            R[e][f] = std::abs(z.real()) < kTransferZero ? 0.0 : z.real();
         }
 }
 
@@ -128,7 +133,7 @@ static void pauli1_fwd(c128 *x)
     x[0] = a + d, x[1] = b + c, x[2] = b - c, x[3] = a - d;
 }
 
-static void pauli_transfer1(const c128 *S, double R[4][4])
+void pauli_transfer1(const c128 *S, double R[4][4])
 {
     for (int f = 0; f < 4; f++) {
         c128 col[4] = {};
@@ -145,7 +150,7 @@ static void pauli_transfer1(const c128 *S, double R[4][4])
             c128 z = sc[e] / 4.0;
             if (e == 2) z *= c128(0, 1);
             if (f == 2) z *= c128(0, -1);
-            R[e][f] = z.real();
+            R[e][f] = std::abs(z.real()) < kTransferZero ? 0.0 : z.real();
         }
     }
 }

@@ -76,6 +76,15 @@ struct TilePlan {
 // tile is again a tile of the pass.
 void append_tile_plan(const std::vector<PassPlan> &plan, int n, int tbmax, TilePlan &out, bool herm = false);
 
+// Real transfer matrices R of a Hermiticity-preserving superoperator S in the Pauli basis of its
+// qubits, for the butterfly form the kernels apply (members to (I, X, D, Z) per qubit, i on the
+// members with an odd number of D components, c = R v, -i back, the same butterflies again).
+// Two qubits: S and R 16 x 16, member index 8 r_a + 4 r_b + 2 c_a + c_b; one qubit: 4 x 4,
+// index 2 r + c.  For a trace-preserving S the first row of R is (1/4, 0, ...) (two qubits) or
+// (1/2, 0, 0, 0) (one qubit), exact in FP32.
+void pauli_transfer(const std::vector<c128> &S, double R[16][16]);
+void pauli_transfer1(const c128 *S, double R[4][4]);
+
 // Dynamic shared memory of a tile kernel for a pass with TB tile bits and an L-bit run.
 size_t tile_smem_bytes(int TB, int L);
 

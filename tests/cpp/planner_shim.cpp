@@ -124,3 +124,21 @@ extern "C" int tile_plan(int n, int kmax, int search, int herm, int tbmax, int n
     *ncoefs = (int)tp.coefs.size();
     return (int)tp.phases.size();
 }
+
+// Real Pauli-basis transfer matrix of a one- or two-qubit superoperator S (complex128,
+// interleaved, 4^k x 4^k row-major) as the plain kernels k_super1 / k_super2 receive it.
+extern "C" void pauli_transfer_k(int k, const double *S, double *R)
+{
+    const int D = 1 << (2 * k);
+    std::vector<c128> s((size_t)D * D);
+    for (int t = 0; t < D * D; t++) s[t] = c128(S[2 * t], S[2 * t + 1]);
+    if (k == 1) {
+        double r[4][4];
+        pauli_transfer1(s.data(), r);
+        for (int i = 0; i < 16; i++) R[i] = r[i / 4][i % 4];
+    } else {
+        double r[16][16];
+        pauli_transfer(s, r);
+        for (int i = 0; i < 256; i++) R[i] = r[i / 16][i % 16];
+    }
+}

@@ -455,3 +455,93 @@ def test_fidelity_of_a_state_with_itself_and_commuting_states():
     p, q = rng.dirichlet(np.ones(4)), rng.dirichlet(np.ones(4))
     d = np.diag(p).astype(np.complex128)
     assert abs(oracle.fidelity(d, [0, 1], np.diag(q)) - np.sum(np.sqrt(p * q))) < 1e-12
+
+
+# ----------------------------------------------------------------------------- noise experiments
+def _oracle_mv(exp):
+    """The oracle replaying one of the paper's noise experiments (Sec. 5.3-5.4): per step the
+    Kraus form of Eq. rhoE4's average on the whole register, then the step's algorithm gates."""
+    rho = exp.rho0()
+    allq = list(range(exp.n))
+    states = [rho.copy()]
+    prev = oracle.set_threads(0)
+    oracle.set_threads(1)  # a few-qubit state: one thread
+    try:
+        for s in range(1, exp.nsteps + 1):
+            oracle.apply_kraus(rho, exp.kraus(s), allq)
+            for u, qs in exp.gates(s):
+                oracle.apply_unitary(rho, u, qs)
+            states.append(rho.copy())
+    finally:
+        oracle.set_threads(prev)
+    return states
+
+
+def test_mv1_noiseless_fidelity_path():
+    """MV1 without noise (caption of the MV1 figure): the fidelity with |0> is 1, drops to 1/sqrt 2
+    after the Hadamard of step 1, stays there, and returns to 1 after the Hadamard of step 3; the
+    state stays pure."""
+    exp = wl.mv_experiment("MV1", "none", nsteps=6)
+    states = _oracle_mv(exp)
+    f = [oracle.fidelity(r, [0], exp.rho0()) for r in states]
+    np.testing.assert_allclose(f, [1, 2 ** -0.5, 2 ** -0.5, 1, 1, 1, 1], atol=1e-12)
+    assert all(abs(oracle.purity(r) - 1) < 1e-12 for r in states)
+
+
+def test_mv2_noiseless_bell_and_return():
+    """MV2 without noise (Sec. 5.3): after CNOT_12 H_1 the state is the Bell state, corners 1/2
+    (golden bell.txt gives the same); the fidelity with |00> is 1/sqrt 2 from step 1 to 3 and
+    1 again after the inverse Bell operator of steps 3-4."""
+    exp = wl.mv_experiment("MV2", "none", nsteps=6)
+    states = _oracle_mv(exp)
+    bell = states[2]
+    for r, c in ((0, 0), (0, 3), (3, 0), (3, 3)):
+        assert abs(bell[r, c] - 0.5) < 1e-12
+    assert abs(np.abs(bell).sum() - 2.0) < 1e-12
+    f = [oracle.fidelity(r, [0, 1], exp.rho0()) for r in states]
+    np.testing.assert_allclose(f, [1, 2 ** -0.5, 2 ** -0.5, 2 ** -0.5, 1, 1, 1], atol=1e-12)
+
+
+def test_mvn_noiseless_ghz_corners():
+    """MVn without noise (Sec. 5.4): after H_1 and CNOT_12 .. CNOT_15 the five qubits are in the GHZ
+    state: the four corners of rho are 1/2 and everything else 0."""
+    exp = wl.mv_experiment("MVn", "none", nsteps=6)
+    rho = _oracle_mv(exp)[5]
+    want = np.zeros((32, 32))
+    for r, c in ((0, 0), (0, 31), (31, 0), (31, 31)):
+        want[r, c] = 0.5
+    np.testing.assert_allclose(rho, want, atol=1e-12)
+
+
+def test_mv2_long_noise_classical_limit():
+    """Sec. 5.2.3: continued noise drives rho to the classical form, all eigenvalues 1/2^n_q
+    (1/4 for MV2), entropy n_q bits, purity 1/4."""
+    exp = wl.mv_experiment("MV2", "xyz", nsteps=300)
+    rho = _oracle_mv(exp)[-1]
+    w = np.linalg.eigvalsh(rho)
+    np.testing.assert_allclose(w, 0.25, atol=1e-4)
+    assert abs(oracle.entropy(rho, [0, 1]) - 2) < 1e-4
+    assert abs(oracle.purity(rho) - 0.25) < 1e-4
+
+
+@pytest.mark.parametrize("name", ["MV1", "MV2", "MVn"])
+def test_mv_noise_step_is_the_pauli_average(name):
+    """One noise step of Eq. rhoE4 on a random state, by the oracle's Kraus sum, against the
+    definition: p rho + sum over the noise paths of (eps p_s / n_p) P rho P, each P a Pauli
+    string written out by Kronecker products (numpy), with Z-only noise leaving the diagonal as
+    it was (Z strings commute with the computational-basis projectors)."""
+    rng = np.random.default_rng(55)
+    for noise in ("xyz", "yz", "z"):
+        exp = wl.mv_experiment(name, noise, nsteps=3)
+        rho = random_rho(rng, exp.n)
+        got = oracle.apply_kraus(rho.copy(), exp.kraus(2), list(range(exp.n)))
+        want = np.zeros_like(rho)
+        for w, hits in exp.noise_terms(2):
+            P = np.ones((1, 1))
+            for q in range(exp.n):
+                a = dict(hits).get(q, 0)
+                P = np.kron(P, (np.eye(2), wl.gate_matrix("X"), wl.gate_matrix("Y"), wl.gate_matrix("Z"))[a])
+            want += w * P @ rho @ P.conj().T
+        np.testing.assert_allclose(got, want, atol=1e-14)
+        if noise == "z":
+            np.testing.assert_allclose(np.diag(got), np.diag(rho), atol=1e-15)

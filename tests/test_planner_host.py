@@ -405,3 +405,58 @@ def test_trace_row_of_two_qubit_transfer_matrices(shim):
         row0 = np.array([cf[off + 8 * f].real for f in range(16)])
         assert abs(row0[0] - 0.25) < 1e-12
         assert np.abs(row0[1:]).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------- plain-path transfer form
+def _pauli_apply_plain(R, x, k):
+    """The plain kernels' arithmetic on one group (k_super1 / k_super2): butterflies per qubit,
+    i on the odd members, c = R v, -i back, the same butterflies.  x: 4^k members, index
+    (row bits, column bits) as 2 r + c (k = 1) or 8 r1 + 4 r2 + 2 c1 + c2 (k = 2)."""
+    x = np.array(x, dtype=np.complex128)
+
+    def fly(v):
+        v = v.copy()
+        quads = [(2, 1, 0)] if k == 1 else [(8, 2, o) for o in (0, 1, 4, 5)] + [(4, 1, o) for o in (0, 2, 8, 10)]
+        for s1, s2, o in quads:
+            a, b, c, d = v[o], v[o + s2], v[o + s1], v[o + s1 + s2]
+            v[o], v[o + s2], v[o + s1], v[o + s1 + s2] = a + d, b + c, b - c, a - d
+        return v
+
+    def odd(e):
+        if k == 1:
+            return e == 2
+        return bool(((e >> 3) & 1) and not ((e >> 1) & 1)) != bool(((e >> 2) & 1) and not (e & 1))
+
+    v = fly(x)
+    v = np.array([1j * v[f] if odd(f) else v[f] for f in range(4 ** k)])
+    c = R @ v
+    c = np.array([-1j * c[e] if odd(e) else c[e] for e in range(4 ** k)])
+    return fly(c)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_plain_transfer_form_reproduces_the_superoperator(shim, k):
+    """For gates (S = U (x) conj U) and Kraus sets, the transfer matrix the library computes for
+    the plain kernels, applied with their butterfly arithmetic, gives S x; for trace-preserving
+    maps its first row is exactly (2^-k, 0, ...) in FP32, so the kernels keep the trace."""
+    rng = np.random.default_rng(1700 + k)
+    d = 1 << k
+    P = ctypes.c_void_p
+    for trial in range(6):
+        if trial % 2 == 0:
+            u = haar_unitary(rng, d)
+            S = np.kron(u, u.conj())
+        else:
+            ks = [np.sqrt(w) * haar_unitary(rng, d) for w in rng.dirichlet(np.ones(3))]
+            S = _superop_kraus(ks)
+        # S's index (row, column) of the member: reorder kron's (r1 c1 | ...) -- np.kron(K, conj K)
+        # indexes (r, c) as r * d + c with r, c the whole row / column labels, i.e. the members'
+        # row bits above their column bits, as the kernels use
+        Sd = np.ascontiguousarray(S, dtype=np.complex128)
+        R = np.zeros((4 ** k) ** 2)
+        shim.pauli_transfer_k(k, Sd.ctypes.data_as(P), R.ctypes.data_as(P))
+        R = R.reshape(4 ** k, 4 ** k)
+        x = rng.standard_normal(4 ** k) + 1j * rng.standard_normal(4 ** k)
+        np.testing.assert_allclose(_pauli_apply_plain(R, x, k), Sd @ x, atol=1e-12)
+        R32 = R.astype(np.float32)
+        assert R32[0, 0] == np.float32(2.0 ** -k) and not R32[0, 1:].any()
