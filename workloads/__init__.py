@@ -30,4 +30,10 @@ from .circuits import (  # noqa: F401
     zero_state,
     mixed_plus_haar_state,
     seed_for,
+    MVExperiment,
+    MV_ALGORITHMS,
+    NOISE_SWITCHES,
+    PAULI_NAMES,
+    mv_experiment,
+    mv_trajectories,
 )

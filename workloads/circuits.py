@@ -289,3 +289,119 @@ def config5_requests(rate: float = 2000.0, duration: float = 60.0, nmin: int = 3
         out.append((t, c))
         j += 1
     return out
+
+
+# ----------------------------------------------------------------------------- multiverse noise experiments
+# The paper's noise studies (Sec. 5.2-5.4; notebooks MV1-Noise, MV2-Noise, MVn-Noise): a short
+# algorithm on 1, 2 or 5 qubits, and at every step the ensemble average of Eq. rhoE4 over n_p
+# noise paths.  The ideal path keeps rho with probability p (the storage case: p = 0.8,
+# eps = 0.2); path k applies, with probability eps p_1 / n_p, a Pauli to one random qubit and,
+# with probability eps p_2 / n_p, Paulis to two distinct random qubits (p_1 = 0.95, p_2 = 0.05;
+# a one-qubit register has only the one-hit case, weight eps / n_p).  The noise operators are
+# drawn once and held fixed.  Switching a Pauli off (the notebooks' ss[i] -> s[0]) replaces it
+# by the identity after the draw, so every noise setting shares the same random structure.
+# This module only draws these inputs; both sides apply them.
+
+PAULI_NAMES = ("I", "X", "Y", "Z")
+NOISE_SWITCHES = {"xyz": (1, 2, 3), "yz": (2, 3), "z": (3,), "none": ()}
+
+MV_ALGORITHMS = {
+    # |0>, Hadamard at step 1, another at step 3, then noise only (caption of the MV1 figure)
+    "MV1": (1, {1: [("H", (0,))], 3: [("H", (0,))]}),
+    # |00>, H on qubit 1 then CNOT_12 (the Bell preparation), later CNOT_12 then H_1 (its
+    # inverse), then noise only (Sec. 5.3, MV2-Noise)
+    "MV2": (2, {1: [("H", (0,))], 2: [("CNOT", (0, 1))], 3: [("CNOT", (0, 1))], 4: [("H", (0,))]}),
+    # |00000>, H_1 then CNOT_12, CNOT_13, CNOT_14, CNOT_15: the GHZ chain (Sec. 5.4, MVn-Noise)
+    "MVn": (5, {1: [("H", (0,))], 2: [("CNOT", (0, 1))], 3: [("CNOT", (0, 2))], 4: [("CNOT", (0, 3))],
+                5: [("CNOT", (0, 4))]}),
+}
+
+
+@dataclass
+class MVExperiment:
+    name: str
+    n: int
+    nsteps: int
+    n_p: int
+    noise: str
+    p: float = 0.8
+    eps: float = 0.2
+    ps: Tuple[float, float] = (0.95, 0.05)
+    algorithm: dict = field(default_factory=dict)
+    hits: list = field(default_factory=list)  # hits[step - 1][k] = (one-hit [(q, a)], two-hit [(q, a), (q, a)])
+
+    def _on(self, a: int) -> int:
+        return a if a in NOISE_SWITCHES[self.noise] else 0
+
+    def noise_terms(self, step: int):
+        """Terms (weight, [(qubit, Pauli index 0..3), ...]) of the noise average at `step` (1-based);
+        the first term is the ideal path.  Weights sum to 1."""
+        terms = [(self.p, [])]
+        for one, two in self.hits[step - 1]:
+            if self.n == 1:
+                terms.append((self.eps / self.n_p, [(q, self._on(a)) for q, a in one]))
+            else:
+                terms.append((self.eps * self.ps[0] / self.n_p, [(q, self._on(a)) for q, a in one]))
+                terms.append((self.eps * self.ps[1] / self.n_p, [(q, self._on(a)) for q, a in two]))
+        return terms
+
+    def pauli_string(self, hits) -> np.ndarray:
+        """The full-register operator of a term's hits (qubit 0 the leftmost Kronecker factor)."""
+        ops = [_FIXED["I"]] * self.n
+        ops = list(ops)
+        for q, a in hits:
+            ops[q] = _FIXED[PAULI_NAMES[a]]
+        m = np.ones((1, 1), dtype=np.complex128)
+        for o in ops:
+            m = np.kron(m, o)
+        return m
+
+    def kraus(self, step: int) -> np.ndarray:
+        """Kraus form of the step's noise average (Eq. rhoE2): sqrt(w) times each term's operator,
+        acting on all qubits 0..n-1 in order."""
+        return np.stack([np.sqrt(w) * self.pauli_string(h) for w, h in self.noise_terms(step)])
+
+    def gates(self, step: int):
+        """Algorithm operators of `step` as (matrix, qubits), applied after the step's noise."""
+        return [(gate_matrix(name), qs) for name, qs in self.algorithm.get(step, [])]
+
+    def psi0(self) -> np.ndarray:
+        v = np.zeros(1 << self.n, dtype=np.complex128)
+        v[0] = 1.0
+        return v
+
+    def rho0(self) -> np.ndarray:
+        return zero_state(self.n)
+
+
+def mv_experiment(name: str, noise: str = "xyz", nsteps: int | None = None, n_p: int = 8,
+                  index: int = 0) -> MVExperiment:
+    """One of the paper's noise experiments with its noise operators drawn (seeded, held fixed)."""
+    n, algo = MV_ALGORITHMS[name]
+    nsteps = nsteps if nsteps is not None else {"MV1": 30, "MV2": 40, "MVn": 24}[name]
+    rng = np.random.Generator(np.random.PCG64(seed_for(6, 10 * index + ("MV1", "MV2", "MVn").index(name))))
+    hits = []
+    for _ in range(nsteps):
+        step = []
+        for _ in range(n_p):
+            q = int(rng.integers(n))
+            one = [(q, int(rng.integers(1, 4)))]
+            two = []
+            if n > 1:
+                q1, q2 = (int(x) for x in rng.choice(n, size=2, replace=False))
+                two = [(q1, int(rng.integers(1, 4))), (q2, int(rng.integers(1, 4)))]
+            step.append((one, two))
+        hits.append(step)
+    return MVExperiment(name, n, nsteps, n_p, noise, algorithm=algo, hits=hits)
+
+
+def mv_trajectories(exp: MVExperiment, nvec: int, index: int = 0) -> np.ndarray:
+    """Sampled paths of the statevector form of the same experiment: choice[step - 1, v] is the
+    index of the noise term (into exp.noise_terms(step)) that vector v takes at that step, drawn
+    with the terms' weights.  The average of the nvec pure states estimates rho."""
+    rng = np.random.Generator(np.random.PCG64(seed_for(7, index)))
+    out = np.zeros((exp.nsteps, nvec), dtype=np.int32)
+    for s in range(1, exp.nsteps + 1):
+        w = np.array([t[0] for t in exp.noise_terms(s)])
+        out[s - 1] = rng.choice(len(w), size=nvec, p=w / w.sum())
+    return out
