@@ -107,6 +107,101 @@ __global__ void k_ens_density(const float2 *__restrict__ psi, int nvec, int n, c
     }
 }
 
+// Tiled form of the same rank-nvec update for n >= 6: rho = Psi^T diag(w) conj(Psi) is an outer
+// product summed over the vectors, so a CTA owns a 64 x 64 tile of rho, stages 16 vectors' 64
+// row amplitudes (times w_v) and 64 column amplitudes in shared memory at a time, and each thread
+// accumulates a 4 x 4 block of the tile in registers: 64 FMAs per 8 shared-memory loads instead of
+// two global loads per 4 FMAs.  rho is Hermitian, so only tiles on or below the diagonal are
+// computed; the one above is written as the conjugate transpose through shared memory.  Tile
+// pairs in the order of pair_blocked's triangle, one per CTA in a grid-stride loop.
+constexpr int kDenT = 64;   // tile edge
+constexpr int kDenV = 16;   // vectors staged per round
+constexpr int kDenThreads = 256;
+
+__global__ void __launch_bounds__(kDenThreads) k_ens_density_tiled(const float2 *__restrict__ psi, int nvec, int n,
+                                                                   const float *__restrict__ w,
+                                                                   float2 *__restrict__ rho)
+{
+    // one buffer: the staged vectors (As, Bs) while a tile accumulates, then the finished tile
+    // (Tt, padded rows) for its mirrored write
+    __shared__ __align__(16) float2 sbuf[kDenT * (kDenT + 1)];
+    float2(*As)[kDenT] = reinterpret_cast<float2(*)[kDenT]>(sbuf);
+    float2(*Bs)[kDenT] = reinterpret_cast<float2(*)[kDenT]>(sbuf + kDenV * kDenT);
+    float2(*Tt)[kDenT + 1] = reinterpret_cast<float2(*)[kDenT + 1]>(sbuf);
+    const uint64_t dim = 1ull << n;
+    const unsigned M = (unsigned)(dim / kDenT);
+    const unsigned npairs = M * (M + 1) / 2;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (unsigned pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        unsigned R, C;  // row-tile R >= column-tile C: pr = R (R + 1) / 2 + C
+        R = (unsigned)((sqrt(8.0 * pr + 1.0) - 1.0) / 2.0);
+        while (R * (R + 1) / 2 > pr) R--;
+        while ((R + 1) * (R + 2) / 2 <= pr) R++;
+        C = pr - R * (R + 1) / 2;
+        const uint64_t r0 = (uint64_t)R * kDenT, c0 = (uint64_t)C * kDenT;
+        float2 acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
+        for (int v0 = 0; v0 < nvec; v0 += kDenV) {
+            __syncthreads();  // the previous round's (or tile's) reads of As / Bs are done
+            for (int e = tid; e < kDenV * kDenT; e += kDenThreads) {
+                const int v = e / kDenT, i = e % kDenT;
+                float2 a = make_float2(0.f, 0.f), b = a;
+                if (v0 + v < nvec) {
+                    const float2 *pv = psi + ((uint64_t)(v0 + v) << n);
+                    const float wv = w[v0 + v];
+                    a = pv[r0 + i];
+                    a = make_float2(wv * a.x, wv * a.y);
+                    b = pv[c0 + i];
+                }
+                As[v][i] = a;
+                Bs[v][i] = b;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int v = 0; v < kDenV; v++) {
+                const float4 a01 = *reinterpret_cast<const float4 *>(&As[v][4 * ty]);
+                const float4 a23 = *reinterpret_cast<const float4 *>(&As[v][4 * ty + 2]);
+                const float4 b01 = *reinterpret_cast<const float4 *>(&Bs[v][4 * tx]);
+                const float4 b23 = *reinterpret_cast<const float4 *>(&Bs[v][4 * tx + 2]);
+                const float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
+                                     make_float2(a23.z, a23.w)};
+                const float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
+                                     make_float2(b23.z, b23.w)};
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {  // acc += a_i conj(b_j)
+                        acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(a[i].y, b[j].y, acc[i][j].x));
+                        acc[i][j].y = fmaf(a[i].y, b[j].x, fmaf(-a[i].x, b[j].y, acc[i][j].y));
+                    }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            float2 *row = rho + (r0 + 4 * ty + i) * dim + c0 + 4 * tx;
+            *reinterpret_cast<float4 *>(row) = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
+            *reinterpret_cast<float4 *>(row + 2) = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
+        }
+        if (R == C) continue;
+        __syncthreads();  // every thread is done reading As / Bs
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) Tt[4 * ty + i][4 * tx + j] = acc[i][j];
+        __syncthreads();
+        // mirror tile (C, R): element (jj, ii) = conj(tile (ii, jj)); consecutive threads take
+        // consecutive columns ii of a mirror row jj
+        for (int e = tid; e < kDenT * kDenT; e += kDenThreads) {
+            const int jj = e / kDenT, ii = e % kDenT;
+            const float2 t = Tt[ii][jj];
+            rho[(c0 + jj) * dim + r0 + ii] = make_float2(t.x, -t.y);
+        }
+    }
+}
+
 __global__ void k_ens_zero(float2 *__restrict__ psi, int n, uint64_t items)
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < items;
@@ -302,8 +397,15 @@ extern "C" qcw_status qcw_ensemble_density(qcw_ensemble *e, const double *weight
     qcw_status st = begin_state_replace(ctx);
     if (st) return st;
     const uint64_t dim = 1ull << e->n;
-    k_ens_density<<<ens_grid(dim * dim, e->nsm), kEnsThreads, 0, ctx->stream>>>(e->psi, e->nvec, e->n, e->d_w,
-                                                                               ctx->rho);
+    if (dim >= (uint64_t)kDenT) {
+        const uint64_t m = dim / kDenT, pairs = m * (m + 1) / 2;
+        const uint64_t cap = (uint64_t)e->nsm * 8;  // 8 CTAs of 256 threads resident per SM
+        k_ens_density_tiled<<<(unsigned)(pairs < cap ? pairs : cap), kDenThreads, 0, ctx->stream>>>(
+            e->psi, e->nvec, e->n, e->d_w, ctx->rho);
+    } else {
+        k_ens_density<<<ens_grid(dim * dim, e->nsm), kEnsThreads, 0, ctx->stream>>>(e->psi, e->nvec, e->n, e->d_w,
+                                                                                   ctx->rho);
+    }
     ENS_CK(cudaGetLastError());
     ctx->launches++;
     ENS_CK(cudaStreamSynchronize(ctx->stream));  // the ensemble may change right after

@@ -113,3 +113,26 @@ def test_density_weights_and_validation(q):
     d.close()
     d3.close()
     e.close()
+
+
+@pytest.mark.parametrize("n,nvec", [(5, 9), (6, 16), (8, 37), (9, 3)])
+def test_density_of_host_vectors_against_the_definition(q, n, nvec):
+    """rho = sum_v w_v |psi_v><psi_v| (Eq. rhoE1's ensemble average) of vectors and weights drawn
+    on the host, against the definition in numpy: below 64 amplitudes one thread per element, from
+    64 on the tiled Hermitian kernel (a single diagonal tile at n = 6; lower tiles and their mirrors
+    at n = 8, 9; a partial last round of vectors for nvec = 37)."""
+    rng = np.random.default_rng(64 + n)
+    psi = _random_vectors(rng, nvec, n)
+    w = rng.uniform(0.1, 1.0, nvec)
+    w /= w.sum()
+    want = np.einsum("v,vr,vc->rc", w, psi, psi.conj())
+    e = q.Ensemble(n, nvec)
+    e.set(psi)
+    d = q.Density(n)
+    e.density(w, d)
+    got = d.get_state()
+    assert np.abs(got - want).max() <= 1e-6
+    assert np.abs(got - got.conj().T).max() <= 1e-7
+    assert abs(d.trace() - 1) <= 1e-6
+    d.close()
+    e.close()
