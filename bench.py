@@ -488,6 +488,7 @@ def run_ours(args):
         extras["batch"] = measure_batch(q2, steps=3, warmup=3)
         extras["serve"] = measure_serve(q2, rate=2000.0, duration=5.0)
 
+    traffic = recorded_traffic(TIMED_KERNEL[args.fused_kernel])
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -500,7 +501,10 @@ def run_ours(args):
                        "qubits": nq, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({8 * 4 ** nq / 2**20:.0f} MiB rho vs 129 MB L2)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": recorded_traffic(TIMED_KERNEL[args.fused_kernel]),
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "achieved_is": "algorithmic bytes (one read and one write of rho, 16 * 4^n) per pass "
+                                        "launch / the launch's event-timed duration",
+                         "dram_gbs": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9,
                          "peak_kind": peak_kind, "kernel": TIMED_KERNEL[args.fused_kernel],
                          "bytes_per_launch": per_launch_bytes,
                          "design_bytes_per_launch": design_pass_bytes(nq, TIMED_KERNEL[args.fused_kernel]),

@@ -695,7 +695,7 @@ static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, 
 {
     const int n = c->n;
     TilePlan tp;
-    append_tile_plan(plan_passes(ops, b, e, n, k, false, PassSearch::BEST), n, tbmax, tp, herm_kernel(c));
+    append_tile_plan(plan_passes(ops, b, e, n, k, false, PassSearch::BEAM), n, tbmax, tp, herm_kernel(c));
     cp.hpass = tp.passes;
     cp.smem = tp.smem;
     for (const FPass &fp : tp.passes) {
@@ -781,7 +781,7 @@ static int auto_k(const std::vector<QOp> &ops, size_t b, size_t e, int n, bool h
     double bc = -1;
     for (int k = 3; k <= 5 && k <= n; k++) {
         TilePlan tp;
-        append_tile_plan(plan_passes(ops, b, e, n, k, true, PassSearch::BEST), n, tbmax, tp, herm);
+        append_tile_plan(plan_passes(ops, b, e, n, k, true, PassSearch::BEAM), n, tbmax, tp, herm);
         const double c = fused_cost(tp, n);
         if (bc < 0 || c < bc) {
             bc = c;

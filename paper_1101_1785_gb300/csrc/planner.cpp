@@ -177,6 +177,67 @@ static size_t absorbable(const std::vector<unsigned> &masks, unsigned Q)
     return taken;
 }
 
+// Beam search over pass sequences (PassSearch::BEAM): returns the candidate set of every pass
+// of the shortest sequence found that absorbs all operations (masks in order).  A partial
+// sequence's remaining operations are what the absorb rule leaves; partial sequences are ranked
+// by how many remain, and identical remainders are kept once.
+constexpr int kBeamWidth = 64;
+constexpr int kBeamBranch = 12;
+
+static std::vector<unsigned> beam_pass_sets(const std::vector<unsigned> &masks, const std::vector<unsigned> &cand)
+{
+    struct Node {
+        std::vector<unsigned> rem;
+        std::vector<unsigned> seq;
+    };
+    std::vector<Node> beam(1);
+    beam[0].rem = masks;
+    for (;;) {
+        std::vector<Node> next;
+        for (const Node &nd : beam) {
+            // the kBeamBranch most absorbing candidate sets (ties: the earlier candidate)
+            std::vector<std::pair<size_t, size_t>> score;  // (absorbed, candidate index)
+            score.reserve(cand.size());
+            for (size_t c = 0; c < cand.size(); c++) score.emplace_back(absorbable(nd.rem, cand[c]), c);
+            const size_t nb = std::min<size_t>(kBeamBranch, score.size());
+            std::partial_sort(score.begin(), score.begin() + nb, score.end(),
+                              [](const std::pair<size_t, size_t> &a, const std::pair<size_t, size_t> &b) {
+                                  return a.first != b.first ? a.first > b.first : a.second < b.second;
+                              });
+            for (size_t j = 0; j < nb; j++) {
+                if (score[j].first == 0) break;
+                const unsigned Q = cand[score[j].second];
+                Node ch;
+                ch.seq = nd.seq;
+                ch.seq.push_back(Q);
+                unsigned blocked = 0;
+                for (unsigned S : nd.rem) {
+                    if ((S & ~Q) || (S & blocked)) {
+                        blocked |= S;
+                        ch.rem.push_back(S);
+                    }
+                }
+                if (ch.rem.empty()) return ch.seq;
+                next.push_back(std::move(ch));
+            }
+        }
+        if (next.empty()) return {};  // nothing absorbs anything: the caller's greedy choice handles it
+        std::stable_sort(next.begin(), next.end(),
+                         [](const Node &a, const Node &b) { return a.rem.size() < b.rem.size(); });
+        beam.clear();
+        for (Node &ch : next) {
+            bool dup = false;
+            for (const Node &kept : beam)
+                if (kept.rem == ch.rem) {
+                    dup = true;
+                    break;
+                }
+            if (!dup) beam.push_back(std::move(ch));
+            if ((int)beam.size() == kBeamWidth) break;
+        }
+    }
+}
+
 std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, size_t end, int n, int kmax,
                                   bool count_only, PassSearch search)
 {
@@ -185,21 +246,30 @@ std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, siz
     std::vector<size_t> rem;
     for (size_t i = begin; i < end; i++) rem.push_back(i);
     const unsigned all = n >= 32 ? ~0u : ((1u << n) - 1u);
-    const std::vector<unsigned> cand = search == PassSearch::BEST ? subsets_of_size(n, kmax < n ? kmax : n)
-                                                                  : std::vector<unsigned>();
-    std::vector<unsigned> masks;
+    const std::vector<unsigned> cand = search != PassSearch::ORDER ? subsets_of_size(n, kmax < n ? kmax : n)
+                                                                   : std::vector<unsigned>();
+    std::vector<unsigned> masks, seq;
+    if (search == PassSearch::BEAM && !cand.empty()) {
+        for (size_t i : rem) masks.push_back(qmask(ops[i]));
+        seq = beam_pass_sets(masks, cand);
+    }
+    size_t npass = 0;
     while (!rem.empty()) {
         unsigned Q = 0, blocked = 0;
         std::vector<size_t> chosen, rest;
         if (!cand.empty()) {
             masks.clear();
             for (size_t i : rem) masks.push_back(qmask(ops[i]));
-            size_t best = 0;
-            for (unsigned C : cand) {
-                const size_t t = absorbable(masks, C);
-                if (t > best) {
-                    best = t;
-                    Q = C;
+            if (npass < seq.size()) {
+                Q = seq[npass];
+            } else {
+                size_t best = 0;
+                for (unsigned C : cand) {
+                    const size_t t = absorbable(masks, C);
+                    if (t > best) {
+                        best = t;
+                        Q = C;
+                    }
                 }
             }
             for (size_t idx = 0; idx < rem.size(); idx++) {
@@ -234,6 +304,7 @@ std::vector<PassPlan> plan_passes(const std::vector<QOp> &ops, size_t begin, siz
                 }
             }
         }
+        npass++;
         PassPlan pp;
         pp.nops = (int)chosen.size();
         for (int q = 0; q < n; q++)

@@ -28,7 +28,11 @@ struct PassPlan {
 // BEST: among all kmax-qubit sets, the one that absorbs the most remaining operations (C(n,
 // kmax) candidates per pass; about a third fewer passes on random circuits, for host time that
 // suits plans that are cached and replayed).
-enum class PassSearch { ORDER, BEST };
+// BEAM: the sequence of kmax-qubit sets chosen by a beam search (the kBeamWidth partial
+// sequences that leave the fewest operations, each extended by its kBeamBranch most absorbing
+// sets) instead of one greedy choice per pass; it finds shorter pass sequences where a greedy
+// choice strands operations that then need passes of their own.
+enum class PassSearch { ORDER, BEST, BEAM };
 
 // Plan ops[begin, end) (all with k <= 2 and no controls) for an n-qubit register.  With
 // count_only the pass / phase structure is produced without composing the superoperators.

@@ -24,7 +24,7 @@ extern "C" int planner_phases(int n, int kmax, int search, int nops, const int *
             o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
     }
     std::vector<PassPlan> plan =
-        plan_passes(ops, 0, ops.size(), n, kmax, false, search ? PassSearch::BEST : PassSearch::ORDER);
+        plan_passes(ops, 0, ops.size(), n, kmax, false, static_cast<PassSearch>(search));
     int np = 0;
     for (size_t p = 0; p < plan.size(); p++) {
         pass_nq[p] = (int)plan[p].Q.size();
@@ -62,7 +62,7 @@ extern "C" int planner_count_only_mismatch(int n, int kmax, int search, int nops
         for (int t = 0; t < dim * dim; t++)
             o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
     }
-    const PassSearch ps = search ? PassSearch::BEST : PassSearch::ORDER;
+    const PassSearch ps = static_cast<PassSearch>(search);
     const std::vector<PassPlan> a = plan_passes(ops, 0, ops.size(), n, kmax, false, ps);
     const std::vector<PassPlan> b = plan_passes(ops, 0, ops.size(), n, kmax, true, ps);
     int bad = a.size() != b.size();
@@ -103,7 +103,7 @@ extern "C" int tile_plan(int n, int kmax, int search, int herm, int tbmax, int n
             o.m[t] = c128(mats[2 * (mat_off[i] + t)], mats[2 * (mat_off[i] + t) + 1]);
     }
     TilePlan tp;
-    append_tile_plan(plan_passes(ops, 0, ops.size(), n, kmax, false, search ? PassSearch::BEST : PassSearch::ORDER),
+    append_tile_plan(plan_passes(ops, 0, ops.size(), n, kmax, false, static_cast<PassSearch>(search)),
                      n, tbmax, tp, herm != 0);
     if ((int)tp.phases.size() > max_phases || (int)tp.passes.size() > max_passes || (int)tp.coefs.size() > max_coefs)
         return -1;

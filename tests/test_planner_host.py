@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
+import workloads as wl
 from tests._helpers import haar_unitary, random_rho
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -129,7 +130,7 @@ def _apply_superop(rho, n, S, qubits):
     return np.einsum(expr, S, t).reshape(rho.shape)
 
 
-@pytest.mark.parametrize("search", [0, 1])
+@pytest.mark.parametrize("search", [0, 1, 2])
 @pytest.mark.parametrize("n,kmax,seed", [(3, 2, 1), (4, 3, 2), (5, 4, 3), (6, 5, 4), (6, 2, 5), (9, 4, 6)])
 def test_planner_replay_matches_oracle(shim, n, kmax, seed, search):
     rng = np.random.default_rng(seed)
@@ -229,7 +230,7 @@ def test_planner_packs_disjoint_work(shim):
     assert len(pass_nq) == 1 and len(phases) == 2
 
 
-@pytest.mark.parametrize("search", [0, 1])
+@pytest.mark.parametrize("search", [0, 1, 2])
 @pytest.mark.parametrize("n,kmax", [(5, 3), (8, 4), (10, 5)])
 def test_count_only_plan_has_the_same_structure(shim, n, kmax, search):
     """The width search plans without composing superoperators; its passes and phases must be
@@ -344,7 +345,7 @@ def _replay_tile_plan(rho, n, phases, cf):
     return flat.reshape(rho.shape)
 
 
-@pytest.mark.parametrize("search", [0, 1])
+@pytest.mark.parametrize("search", [0, 1, 2])
 @pytest.mark.parametrize("n,kmax,herm,seed", [(6, 2, True, 11), (6, 4, True, 12), (5, 3, False, 13), (7, 5, True, 14)])
 def test_tile_plan_coefficients_replay_matches_oracle(shim, n, kmax, herm, seed, search):
     """The packed coefficients of every phase kind, applied with the kernels' arithmetic."""
@@ -374,6 +375,30 @@ def test_best_search_packs_no_more_passes_than_order(shim):
     _, best = _plan(shim, n, 4, ops, 1)
     assert len(best) <= len(order)
     assert len(best) < 0.9 * len(order)
+
+
+def test_beam_search_packs_no_more_passes_than_best(shim):
+    """The beam search over pass sequences never needs more passes than the greedy
+    best-absorption choice (its first partial sequence is the greedy one), on random circuits and
+    on the 100-gate segments of the 14-qubit benchmark circuit at width 5."""
+    rng = np.random.default_rng(78)
+    for n, kmax in ((10, 4), (9, 5)):
+        ops = _random_ops(rng, n, 300)
+        _, best = _plan(shim, n, kmax, ops, 1)
+        _, beam = _plan(shim, n, kmax, ops, 2)
+        assert len(beam) <= len(best)
+    c = wl.config3_circuit()
+    bounds = [len(c.gate_prefix(g).ops) for g in range(0, 1001, 100)]
+    tot_best = tot_beam = 0
+    for i in range(10):
+        seg = [(("u" if o.kind == "gate" else "k"), o.qubits, o.mats[0] if o.kind == "gate" else list(o.mats))
+               for o in c.ops[bounds[i]:bounds[i + 1]]]
+        _, best = _plan(shim, 14, 5, seg, 1)
+        _, beam = _plan(shim, 14, 5, seg, 2)
+        assert len(beam) <= len(best)
+        tot_best += len(best)
+        tot_beam += len(beam)
+    print(f"benchmark circuit at width 5: {tot_best} passes (greedy best), {tot_beam} (beam)")
 
 
 def test_trace_row_of_two_qubit_transfer_matrices(shim):
