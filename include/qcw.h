@@ -119,6 +119,17 @@ QCW_API qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which);
  * Flushes queued work first.  QCW_EINVAL if stall_tile < -1. */
 QCW_API qcw_status qcw_set_fused_wait_limit(qcw_ctx *ctx, unsigned polls, int stall_tile);
 
+/* Validation mode (off by default; on for every new context when the environment variable
+ * QCW_VALIDATE is set to anything but 0).  When on, every apply call checks its matrices before
+ * queueing anything: gates must be unitary (U^dagger U = I within 1e-6; the paper's operators
+ * are unitary, Sec. 3), Kraus sets must not increase the trace (largest eigenvalue of
+ * sum K^dagger K at most 1 + 1e-6; Eq. rhoE1's ensemble keeps it, trace-decreasing sets stay
+ * allowed), and qcw_set_state / qcw_set_state_c64 inputs must be Hermitian with unit trace
+ * (within 1e-6; Sec. 5.2) -- the default fused kernel keeps only the Hermitian part of rho.
+ * Violations return QCW_EINVAL with the state unchanged.  The checks run on the host, O(4^n)
+ * for a state and O(d^3) per matrix. */
+QCW_API qcw_status qcw_set_validation(qcw_ctx *ctx, int on);
+
 /* Device pointer of rho and the context's stream (borrowed; valid until destroy).  Flushes
  * queued work and completes the matrix first (the HERM_WS pass keeps only the lower triangle
  * r >= c current between readouts): the buffer holds all of rho for work ordered on the

@@ -40,6 +40,7 @@ SIGNATURES = {
     "qcw_create_from_ptr": (I, [I, P, P, PP]),
     "qcw_destroy": (I, [P]),
     "qcw_set_mode": (I, [P, I, I]),
+    "qcw_set_validation": (I, [P, I]),
     "qcw_set_fused_kernel": (I, [P, I]),
     "qcw_set_fused_wait_limit": (I, [P, ctypes.c_uint, I]),
     "qcw_get_device_state": (I, [P, PP, PP]),
@@ -268,6 +269,10 @@ class Density:
     # ---------------------------------------------------------------- configuration / state
     def set_mode(self, mode: int, fuse_k: int = 0):
         check(lib().qcw_set_mode(self.h, int(mode), int(fuse_k)), "qcw_set_mode")
+
+    def set_validation(self, on: bool = True):
+        """Check unitarity, Kraus trace and Hermitian states on every call (QCW_EINVAL if not)."""
+        check(lib().qcw_set_validation(self.h, int(bool(on))), "qcw_set_validation")
 
     def set_fused_kernel(self, which: int):
         """0 = auto (warp-specialised Hermitian from 6 qubits), 1 = one CTA per tile (no symmetry

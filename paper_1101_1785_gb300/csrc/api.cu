@@ -1,6 +1,7 @@
 // C ABI of the qcw library: argument checks, context lifetime, the plain (one launch per
 // operation) path and the FP64 readouts.  The fused path lives in fused.cu / planner.cpp.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -66,6 +67,56 @@ static bool all_finite(const double *a, size_t cnt)
     for (size_t i = 0; i < cnt; i++)
         if (!std::isfinite(a[i])) return false;
     return true;
+}
+
+// ------------------------------------------------------------------ validation (qcw_set_validation)
+// The paper's gate operators are unitary (Sec. 3) and its noise ensembles keep the trace
+// (Eq. rhoE1: sum of the path weights is 1); a Kraus set may also lose trace, never gain it.  A
+// state is Hermitian with unit trace (Sec. 5.2).  Tolerance 1e-6 throughout.
+constexpr double kValidTol = 1e-6;
+
+static bool is_unitary(const double *u, int d)
+{
+    const c128 *U = reinterpret_cast<const c128 *>(u);
+    for (int i = 0; i < d; i++)
+        for (int j = 0; j < d; j++) {
+            c128 g = 0;  // (U^dagger U)_ij
+            for (int l = 0; l < d; l++) g += std::conj(U[l * d + i]) * U[l * d + j];
+            if (std::abs(g - c128(i == j ? 1.0 : 0.0, 0.0)) > kValidTol) return false;
+        }
+    return true;
+}
+
+// sum_j K_j^dagger K_j <= I (its largest eigenvalue at most 1 + tolerance).
+static bool kraus_keeps_or_loses_trace(const double *ks, int nk, int d)
+{
+    const c128 *K = reinterpret_cast<const c128 *>(ks);
+    std::vector<c128> M((size_t)d * d, c128(0, 0));
+    for (int t = 0; t < nk; t++)
+        for (int i = 0; i < d; i++)
+            for (int j = 0; j < d; j++)
+                for (int l = 0; l < d; l++)
+                    M[(size_t)i * d + j] += std::conj(K[(size_t)t * d * d + l * d + i]) * K[(size_t)t * d * d + l * d + j];
+    std::vector<double> w(d);
+    herm_eig(M.data(), d, w.data(), nullptr);
+    return w[d - 1] <= 1.0 + kValidTol;
+}
+
+template <typename T>
+static bool is_density(const T *rho, int n)
+{
+    const size_t dim = (size_t)1 << n;
+    double tr_re = 0, tr_im = 0;
+    for (size_t i = 0; i < dim; i++) {
+        tr_re += rho[2 * (i * dim + i)];
+        tr_im += rho[2 * (i * dim + i) + 1];
+        for (size_t j = 0; j < i; j++) {
+            const T *a = rho + 2 * (i * dim + j), *b = rho + 2 * (j * dim + i);
+            if (std::fabs((double)a[0] - (double)b[0]) > kValidTol || std::fabs((double)a[1] + (double)b[1]) > kValidTol)
+                return false;
+        }
+    }
+    return std::fabs(tr_re - 1.0) <= kValidTol && std::fabs(tr_im) <= kValidTol;
 }
 
 static qcw_status check_qubits(int n, const int *qs, int k, const int *ctrl, int nc)
@@ -316,6 +367,8 @@ static void ctx_free(qcw_ctx *c)
 
 static qcw_status ctx_common(qcw_ctx *c)
 {
+    const char *v = getenv("QCW_VALIDATE");
+    c->validate = v && v[0] && v[0] != '0';
     CK(cudaGetDevice(&c->dev));
     CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
     c->red_blocks = reduce_blocks(c->nsm);
@@ -384,6 +437,13 @@ extern "C" qcw_status qcw_destroy(qcw_ctx *ctx)
 }
 
 extern "C" int qcw_nqubits(const qcw_ctx *ctx) { return ctx ? ctx->n : -1; }
+
+extern "C" qcw_status qcw_set_validation(qcw_ctx *ctx, int on)
+{
+    CHECK_CTX(ctx);
+    ctx->validate = on != 0;
+    return QCW_OK;
+}
 
 extern "C" qcw_status qcw_set_fused_kernel(qcw_ctx *ctx, int which)
 {
@@ -484,6 +544,8 @@ extern "C" qcw_status qcw_set_state(qcw_ctx *ctx, const double *rho_c128)
 {
     CHECK_CTX(ctx);
     if (!rho_c128) return set_error(QCW_EINVAL, "null state");
+    if (ctx->validate && !is_density(rho_c128, ctx->n))
+        return set_error(QCW_EINVAL, "state is not Hermitian with unit trace (validation)");
     qcw_status st = ensure_staging(ctx);
     if (st) return st;
     ctx->queue.clear();
@@ -507,6 +569,8 @@ extern "C" qcw_status qcw_set_state_c64(qcw_ctx *ctx, const float *rho_c64)
 {
     CHECK_CTX(ctx);
     if (!rho_c64) return set_error(QCW_EINVAL, "null state");
+    if (ctx->validate && !is_density(rho_c64, ctx->n))
+        return set_error(QCW_EINVAL, "state is not Hermitian with unit trace (validation)");
     ctx->queue.clear();
     ctx->half = false;
     ctx->state_ver++;
@@ -546,6 +610,7 @@ extern "C" qcw_status qcw_apply_gate1(qcw_ctx *ctx, const double u[8], int targe
     qcw_status st = check_qubits(ctx->n, &target, 1, controls, ncontrols);
     if (st) return st;
     if (!all_finite(u, 8)) return set_error(QCW_EINVAL, "non-finite matrix entry");
+    if (ctx->validate && !is_unitary(u, 2)) return set_error(QCW_EINVAL, "gate is not unitary (validation)");
     QOp op;
     op.kind = 0;
     op.k = 1;
@@ -565,6 +630,7 @@ extern "C" qcw_status qcw_apply_gate2(qcw_ctx *ctx, const double u[32], int q1, 
     qcw_status st = check_qubits(ctx->n, qs, 2, controls, ncontrols);
     if (st) return st;
     if (!all_finite(u, 32)) return set_error(QCW_EINVAL, "non-finite matrix entry");
+    if (ctx->validate && !is_unitary(u, 4)) return set_error(QCW_EINVAL, "gate is not unitary (validation)");
     QOp op;
     op.kind = 0;
     op.k = 2;
@@ -585,6 +651,7 @@ extern "C" qcw_status qcw_apply_gate(qcw_ctx *ctx, const double *u, const int *q
     if (st) return st;
     size_t cnt = (size_t)1 << (2 * k);
     if (!all_finite(u, 2 * cnt)) return set_error(QCW_EINVAL, "non-finite matrix entry");
+    if (ctx->validate && !is_unitary(u, 1 << k)) return set_error(QCW_EINVAL, "gate is not unitary (validation)");
     QOp op;
     op.kind = 0;
     op.k = k;
@@ -604,6 +671,8 @@ extern "C" qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkr
     if (st) return st;
     size_t cnt = (size_t)nkraus << (2 * k);
     if (!all_finite(kraus, 2 * cnt)) return set_error(QCW_EINVAL, "non-finite matrix entry");
+    if (ctx->validate && !kraus_keeps_or_loses_trace(kraus, nkraus, 1 << k))
+        return set_error(QCW_EINVAL, "Kraus set increases the trace (validation)");
     QOp op;
     op.kind = k <= 2 ? 1 : 2;
     op.k = k;
@@ -613,7 +682,8 @@ extern "C" qcw_status qcw_apply_kraus(qcw_ctx *ctx, const double *kraus, int nkr
     return submit(ctx, std::move(op));
 }
 
-qcw_status qcw::convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out)
+qcw_status qcw::convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out,
+                            bool validate)
 {
     if (nops < 0 || (nops > 0 && (!ops || !matrices))) return set_error(QCW_EINVAL, "bad op list");
     for (int i = 0; i < nops; i++) {  // validate everything first: all or nothing
@@ -625,6 +695,8 @@ qcw_status qcw::convert_ops(int n, const qcw_op *ops, int nops, const double *ma
             if (st) return st;
             if (!all_finite(matrices + o.offset, (size_t)2 << (2 * o.k)))
                 return set_error(QCW_EINVAL, "non-finite matrix entry");
+            if (validate && !is_unitary(matrices + o.offset, 1 << o.k))
+                return set_error(QCW_EINVAL, "gate is not unitary (validation)");
         } else if (o.kind == QCW_OP_KRAUS) {
             if (o.k < 1 || o.k > 2) return set_error(QCW_EINVAL, "channels act on 1 or 2 qubits");
             if (o.nkraus < 1 || o.nkraus > QCW_MAX_KRAUS) return set_error(QCW_EINVAL, "nkraus out of range");
@@ -632,6 +704,8 @@ qcw_status qcw::convert_ops(int n, const qcw_op *ops, int nops, const double *ma
             if (st) return st;
             if (!all_finite(matrices + o.offset, ((size_t)2 * o.nkraus) << (2 * o.k)))
                 return set_error(QCW_EINVAL, "non-finite matrix entry");
+            if (validate && !kraus_keeps_or_loses_trace(matrices + o.offset, o.nkraus, 1 << o.k))
+                return set_error(QCW_EINVAL, "Kraus set increases the trace (validation)");
         } else {
             return set_error(QCW_EINVAL, "bad op kind");
         }
@@ -658,7 +732,7 @@ extern "C" qcw_status qcw_apply_ops(qcw_ctx *ctx, const qcw_op *ops, int nops, c
 {
     CHECK_CTX(ctx);
     std::vector<QOp> conv;
-    qcw_status st = convert_ops(ctx->n, ops, nops, matrices, conv);
+    qcw_status st = convert_ops(ctx->n, ops, nops, matrices, conv, ctx->validate);
     if (st) return st;
     for (QOp &op : conv) {
         st = submit(ctx, std::move(op));

@@ -122,6 +122,7 @@ struct qcw_ctx {
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
     int mode = QCW_MODE_PLAIN;
+    bool validate = false;  // qcw_set_validation: check unitarity, Kraus trace, Hermitian states
     int fuse_k = 0;
     int fused_kernel = QCW_FUSED_KERNEL_AUTO;
     // reduction scratch: per-block partials and a small result block (+ pinned mirror)
@@ -184,7 +185,8 @@ qcw_status ensure_full(qcw_ctx *c);
 qcw_status begin_state_replace(qcw_ctx *c);
 // Validate an op list against an n-qubit register and convert it to queued operations
 // (Kraus sets become superoperators); nothing is appended on error.
-qcw_status convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out);
+qcw_status convert_ops(int n, const qcw_op *ops, int nops, const double *matrices, std::vector<QOp> &out,
+                       bool validate = false);
 qcw_status set_error(qcw_status st, const std::string &msg);
 // Raise a kernel's max dynamic shared memory on the current device to at least `bytes`.  The
 // attribute is process-wide per function and device, so it only ever grows.

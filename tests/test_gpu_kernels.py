@@ -331,3 +331,44 @@ def test_kraus_channels_on_three_and_four_qubits(q, mode, k):
     assert np.abs(got - want).max() <= 1e-5
     assert abs(d.trace() - oracle.trace(want)) <= 1e-6
     d.close()
+
+
+def test_validation_mode(q):
+    """Off by default (a non-unitary matrix is applied as given); on, non-unitary gates, Kraus
+    sets that increase the trace and states that are not Hermitian with unit trace are rejected
+    with QCW_EINVAL and the state is unchanged; unitary gates, trace-preserving and trace-decreasing
+    Kraus sets and proper states pass, in plain and fused mode and through qcw_apply_ops."""
+    n = 3
+    rng = np.random.default_rng(91)
+    d = q.Density(n)
+    d.apply_gate1(2.0 * np.eye(2), 0)  # not validated: accepted
+    d.reset()
+    for mode in (q.QCW_MODE_PLAIN, q.QCW_MODE_FUSED):
+        d.set_mode(mode, 0)
+        d.set_validation(True)
+        rho = random_rho(rng, n)
+        d.set_state(rho)
+        bad = [lambda: d.apply_gate1(2.0 * np.eye(2), 0),
+               lambda: d.apply_gate2(1.1 * np.eye(4), 0, 1),
+               lambda: d.apply_gate(1.01 * np.eye(8), [0, 1, 2]),
+               lambda: d.apply_kraus(np.stack([np.eye(2), 0.1 * np.eye(2)]), [1]),
+               lambda: d.apply_op(wl.Op("gate", (2,), np.array([[[1.0, 0.0], [0.5, 1.0]]]))),
+               lambda: d.set_state(rho + 1e-3 * np.triu(np.ones((8, 8)), 1)),
+               lambda: d.set_state(1.01 * rho)]
+        for f in bad:
+            with pytest.raises(q.QcwError) as e:
+                f()
+            assert e.value.status == q.QCW_EINVAL
+        assert np.abs(d.get_state() - rho).max() <= 1e-6
+        u = haar_unitary(rng, 2)
+        d.apply_gate1(u, 1)
+        d.apply_kraus(wl.kraus_ad(0.1), [2])
+        d.apply_kraus(np.stack([np.sqrt(0.5) * np.eye(2)]), [0])  # trace-decreasing: allowed
+        want = rho.copy()
+        oracle.apply_unitary(want, u, [1])
+        oracle.apply_kraus(want, wl.kraus_ad(0.1), [2])
+        oracle.apply_kraus(want, np.stack([np.sqrt(0.5) * np.eye(2)]), [0])
+        assert np.abs(d.get_state() - want).max() <= 1e-5
+        d.set_validation(False)
+        d.reset()
+    d.close()
