@@ -54,6 +54,7 @@ static_assert(sizeof(WsParams) <= 32000, "kernel parameter block limit");
 struct CachedPlan {
     uint64_t hash = 0;
     int n = 0, k = 0, tb = 0;
+    bool beam = false;  // passes from the beam search (else the greedy best-absorption choice)
     std::vector<QOp> ops;  // exact copy for verification
     std::vector<FPass> hpass;
     std::vector<int> grid;  // tiles per pass
@@ -691,11 +692,13 @@ static bool ws_pass(const qcw_ctx *c, const FPass &fp)
 }
 
 static qcw_status build_plan(qcw_ctx *c, const std::vector<QOp> &ops, size_t b, size_t e, int k, int tbmax,
-                             CachedPlan &cp)
+                             CachedPlan &cp, bool beam)
 {
     const int n = c->n;
     TilePlan tp;
-    append_tile_plan(plan_passes(ops, b, e, n, k, false, PassSearch::BEAM), n, tbmax, tp, herm_kernel(c));
+    cp.beam = beam;
+    append_tile_plan(plan_passes(ops, b, e, n, k, false, beam ? PassSearch::BEAM : PassSearch::BEST), n, tbmax, tp,
+                     herm_kernel(c));
     cp.hpass = tp.passes;
     cp.smem = tp.smem;
     for (const FPass &fp : tp.passes) {
@@ -781,7 +784,7 @@ static int auto_k(const std::vector<QOp> &ops, size_t b, size_t e, int n, bool h
     double bc = -1;
     for (int k = 3; k <= 5 && k <= n; k++) {
         TilePlan tp;
-        append_tile_plan(plan_passes(ops, b, e, n, k, true, PassSearch::BEAM), n, tbmax, tp, herm);
+        append_tile_plan(plan_passes(ops, b, e, n, k, true, PassSearch::BEST), n, tbmax, tp, herm);
         const double c = fused_cost(tp, n);
         if (bc < 0 || c < bc) {
             bc = c;
@@ -792,6 +795,9 @@ static int auto_k(const std::vector<QOp> &ops, size_t b, size_t e, int n, bool h
 }
 
 static const size_t kMaxCached = 64;
+// Registers from this size up get beam-searched plans for segments that are replayed (a pass
+// there costs at least ~10 us, so the planning time pays back over a few replays).
+constexpr int kBeamMinQubits = 10;
 
 // last: nothing follows this segment in the flush, so its last pass (if warp-specialised) also
 // leaves the purity partials of the resulting rho.
@@ -852,13 +858,33 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e, bool last)
         cp.k = k;
         cp.tb = tbmax;
         cp.ops.assign(c->queue.begin() + b, c->queue.begin() + e);
-        qcw_status st = build_plan(c, c->queue, b, e, k, tbmax, cp);
+        qcw_status st = build_plan(c, c->queue, b, e, k, tbmax, cp, false);
         if (st) {
             release_plan(cp);
             return st;
         }
         rt->cache.push_back(std::move(cp));
         hit = &rt->cache.back();
+    } else if (!hit->beam && n >= kBeamMinQubits && !trial) {
+        // The segment came back, so its plan is replayed: its planning time is paid once and the
+        // passes it saves on every replay, so it is re-planned now with the beam search.  Work
+        // still in flight may read the old plan's buffers.
+        cudaError_t se = cudaStreamSynchronize(c->stream);
+        if (se != cudaSuccess) return cuda_error(se, "stream");
+        CachedPlan np;
+        np.hash = hit->hash;
+        np.n = hit->n;
+        np.k = hit->k;
+        np.tb = hit->tb;
+        np.ops = std::move(hit->ops);
+        qcw_status st = build_plan(c, c->queue, b, e, k, tbmax, np, true);
+        if (st) {
+            release_plan(np);
+            hit->ops.assign(c->queue.begin() + b, c->queue.begin() + e);
+            return st;
+        }
+        release_plan(*hit);
+        *hit = std::move(np);
     }
     hit->last_use = ++rt->tick;
 
