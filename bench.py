@@ -16,8 +16,9 @@ accuracy replay of one step against the complex128 oracle's stored readouts of t
 circuit; the oracle itself timed on a warm sample on every host core and on one; and, at one
 GPU, three sub-measurements -- the 12-qubit depolarising circuit on the plain path (one launch
 per gate and per channel, GB/s per launch), the 512-circuit batch in one persistent launch
-against the one-circuit-at-a-time loop, and 5 s of the Poisson request stream through the
-continuous-batching server (p50 / p99 latency, req/s) against the same loop.
+against the one-circuit-at-a-time loop, 5 s of the Poisson request stream through the
+continuous-batching server (p50 / p99 latency, req/s) against the same loop, and the multiverse
+ensemble's density kernel at 12-14 qubits.
 ``--impl reference`` times the CPU oracle on a bounded sample of the same workload.
 """
 
@@ -58,10 +59,11 @@ def parse_args():
     ap.add_argument("--cpu-gates", type=int, default=3, help="gates of the timed oracle sample (all cores)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the untimed accuracy leg and the plain / batch / serve sub-measurements")
-    ap.add_argument("--workload", default="circuit14", choices=["circuit14", "plain12", "batch", "serve"],
+    ap.add_argument("--workload", default="circuit14", choices=["circuit14", "plain12", "batch", "serve", "ensemble"],
                     help="circuit14: the 14-qubit benchmark (default); plain12: the 12-qubit depolarising circuit "
                          "on the plain path, one launch per gate and per channel; batch: 512 circuits of 4..10 "
-                         "qubits in one launch; serve: Poisson request stream through the continuous-batching server")
+                         "qubits in one launch; serve: Poisson request stream through the continuous-batching server; "
+                         "ensemble: the multiverse ensemble's density kernel")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--fused-kernel", default="auto", choices=["auto", "tile", "herm", "herm_ws", "herm_tc"],
@@ -222,34 +224,33 @@ def recorded_traffic(kernel):
 
 # ----------------------------------------------------------------------------- oracle timing
 def oracle_timed(ngates: int, steps: int = 1, warmup: int = 0, one_core: bool = False):
-    """The oracle as it stands on bounded, warm samples of the benchmark circuit.  The first gate
-    (with its AD + PD channels) runs untimed on every core to touch the state's pages; then each
-    of `warmup` + `steps` samples runs the next `ngates` gates on every core (the first `warmup`
-    untimed), and with one_core the gate after those runs on one thread.  Returns (seconds per
-    timed sample, threads used, one-thread seconds or None)."""
+    """The oracle as it stands on a bounded, warm sample of the benchmark circuit: the ops of gates
+    2 .. ngates + 1 (each gate with its AD + PD channels).  The first gate runs once, untimed, on
+    every core to touch the 4 GiB state's pages; then the sample runs warmup + steps times on every
+    core (the first `warmup` untimed) -- the same operations each time, so every timing covers the
+    same work -- and with one_core the sample's first gate once more on one thread.  Returns
+    (seconds per timed sample, threads used, one-thread seconds or None)."""
     import oracle
     import workloads as wl
 
     c = wl.config3_circuit(n=N_QUBITS, ngates=N_GATES)
     nthreads = os.cpu_count() or 1
     used = oracle.set_threads(nthreads)
-    bounds = [len(c.gate_prefix(g).ops) for g in range(0, N_GATES + 1)]
+    b1, b2, bn = (len(c.gate_prefix(g).ops) for g in (1, 2, 1 + ngates))
     rho = oracle.initial_state(c)
-    oracle.run_circuit(c, rho, c.ops[:bounds[1]])
-    g = 1
+    oracle.run_circuit(c, rho, c.ops[:b1])
     times = []
     for i in range(warmup + steps):
         t0 = time.perf_counter()
-        oracle.run_circuit(c, rho, c.ops[bounds[g]:bounds[g + ngates]])
+        oracle.run_circuit(c, rho, c.ops[b1:bn])
         dt = time.perf_counter() - t0
-        g += ngates
         if i >= warmup:
             times.append(dt)
     one = None
     if one_core:
         oracle.set_threads(1)
         t0 = time.perf_counter()
-        oracle.run_circuit(c, rho, c.ops[bounds[g]:bounds[g + 1]])
+        oracle.run_circuit(c, rho, c.ops[b1:b2])
         one = time.perf_counter() - t0
         oracle.set_threads(nthreads)
     del rho
@@ -261,8 +262,8 @@ def cpu_baseline_legs(ngates: int):
     times, used, one = oracle_timed(ngates, 1, 0, one_core=True)
     dt = times[0]
     sample = (f"gates 2..{ngates + 1} of the 1000-gate 14-qubit circuit with their AD+PD channels on the complex128 "
-              f"oracle, {used} host threads, after one untimed warm-up gate ({dt:.1f} s); then gate {ngates + 2} on "
-              f"one thread ({one:.1f} s)")
+              f"oracle, {used} host threads, after one untimed warm-up gate ({dt:.1f} s); then gate 2 again on one "
+              f"thread ({one:.1f} s)")
     return {"value": ngates / dt, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
             "one_core": {"value": 1.0 / one, "unit": UNIT, "cores": 1, "seconds": one}}
 
@@ -279,8 +280,8 @@ def run_reference(args):
     elapsed = time.perf_counter() - t0
     total = sum(times)
     value = ngates * args.steps / total
-    sample = (f"{ngates} consecutive gates of the 1000-gate 14-qubit circuit with their AD+PD channels per step "
-              f"(from gate 2 on, after one untimed warm-up gate), complex128 oracle on {threads} host threads")
+    sample = (f"gates 2..{ngates + 1} of the 1000-gate 14-qubit circuit with their AD+PD channels per step (the same "
+              f"operations each step, after one untimed warm-up gate), complex128 oracle on {threads} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -446,7 +447,7 @@ def run_ours(args):
     d2.set_mode(q.QCW_MODE_FUSED, args.fuse_k)
     d2.set_fused_kernel({"auto": 0, "tile": 1, "herm": 2, "herm_ws": 3, "herm_tc": 4}[args.fused_kernel])
     ctxs = (d, d2)
-    for k in range(4):  # both contexts planned and tuned
+    for k in range(6):  # both contexts planned, tuned and re-planned for replay (three steps each)
         gpu_step(ctxs[k % 2], packed, host.data_ptr())
     barrier()
     t0 = time.perf_counter()
@@ -487,6 +488,7 @@ def run_ours(args):
         extras["plain12"] = measure_plain12(q2, steps=2, warmup=1)
         extras["batch"] = measure_batch(q2, steps=3, warmup=3)
         extras["serve"] = measure_serve(q2, rate=2000.0, duration=5.0)
+        extras["ensemble_density"] = measure_ensemble(q2)
 
     traffic = recorded_traffic(TIMED_KERNEL[args.fused_kernel])
     if rank == 0:
@@ -614,6 +616,44 @@ def measure_plain12(q, steps=2, warmup=1):
     return out
 
 
+def measure_ensemble(q, sizes=((12, 64), (12, 256), (13, 64), (14, 16), (14, 64)), reps=5):
+    """The multiverse ensemble's density rho = sum_v w_v |psi_v><psi_v| (the paper's ensemble
+    average, formed on the GPU from nvec seeded random unit vectors with equal weights): event
+    time on the density context's stream, best of `reps` after one warm-up.  Algorithmic unit:
+    one write of rho (8 * 4^n bytes) and 8 nvec FP32 flops on half of its elements."""
+    import numpy as np
+    import torch
+
+    peaks, _ = load_peaks()
+    out = []
+    for n, nvec in sizes:
+        rng = np.random.default_rng(n * 1000 + nvec)
+        psi = rng.standard_normal((nvec, 1 << n)) + 1j * rng.standard_normal((nvec, 1 << n))
+        psi /= np.linalg.norm(psi, axis=1, keepdims=True)
+        e = q.Ensemble(n, nvec)
+        e.set(psi)
+        d = q.Density(n)
+        _, sp = d.device_state()
+        st = torch.cuda.ExternalStream(sp)
+        w = np.full(nvec, 1.0 / nvec)
+        e.density(w, d)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            e.density(w, d)
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = min(ts)
+        flops = 8.0 * nvec * 4 ** n / 2
+        out.append({"qubits": n, "vectors": nvec, "ms": ms, "write_floor_ms": 8 * 4 ** n / (float(peaks["hbm_gbs"]) * 1e9) * 1e3,
+                    "tflops_fp32": flops / (ms / 1e3) / 1e12, "trace_err": abs(d.trace().real - 1)})
+        d.close()
+        e.close()
+    return out
+
+
 def measure_batch(q, steps=3, warmup=3):
     import numpy as np
     import torch
@@ -737,6 +777,9 @@ def _standalone(args, what):
     elif what == "batch":
         r = measure_batch(q, steps=args.steps, warmup=args.warmup)
         r.update({"n_gpus": 1, "higher_is_better": True, "dtype": "c64", "data": "synthetic"})
+    elif what == "ensemble":
+        r = {"metric": "ensemble density: ms per rho = sum_v w_v |psi_v><psi_v|", "unit": "ms", "n_gpus": 1,
+             "higher_is_better": False, "dtype": "c64", "data": "synthetic", "sizes": measure_ensemble(q)}
     else:
         r = measure_serve(q, rate=args.rate, duration=args.duration)
         r.update({"n_gpus": 1, "higher_is_better": True, "dtype": "c64", "data": "synthetic"})
@@ -747,7 +790,7 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("plain12", "batch", "serve"):
+    elif args.workload in ("plain12", "batch", "serve", "ensemble"):
         _standalone(args, args.workload)
     else:
         run_ours(args)

@@ -13,6 +13,7 @@ struct qcw_ensemble {
     float2 *psi = nullptr;  // nvec x 2^n
     int *d_choice = nullptr;
     float *d_w = nullptr;
+    unsigned *d_err = nullptr;  // error word of the tensor-core density (a bounded wait ran out)
     void *d_stage = nullptr;  // complex128 staging, one vector
     cudaStream_t stream = nullptr;
 };
@@ -118,9 +119,11 @@ constexpr int kDenT = 64;   // tile edge
 constexpr int kDenV = 16;   // vectors staged per round
 constexpr int kDenThreads = 256;
 
+// diag_blocks: only the 64 x 64 tiles inside the 128 x 128 blocks on the diagonal (three lower
+// tiles per block; the tensor-core kernel does the rest).
 __global__ void __launch_bounds__(kDenThreads) k_ens_density_tiled(const float2 *__restrict__ psi, int nvec, int n,
                                                                    const float *__restrict__ w,
-                                                                   float2 *__restrict__ rho)
+                                                                   float2 *__restrict__ rho, int diag_blocks)
 {
     // one buffer: the staged vectors (As, Bs) while a tile accumulates, then the finished tile
     // (Tt, padded rows) for its mirrored write
@@ -130,14 +133,20 @@ __global__ void __launch_bounds__(kDenThreads) k_ens_density_tiled(const float2 
     float2(*Tt)[kDenT + 1] = reinterpret_cast<float2(*)[kDenT + 1]>(sbuf);
     const uint64_t dim = 1ull << n;
     const unsigned M = (unsigned)(dim / kDenT);
-    const unsigned npairs = M * (M + 1) / 2;
+    const unsigned npairs = diag_blocks ? 3 * (M / 2) : M * (M + 1) / 2;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     for (unsigned pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
-        unsigned R, C;  // row-tile R >= column-tile C: pr = R (R + 1) / 2 + C
-        R = (unsigned)((sqrt(8.0 * pr + 1.0) - 1.0) / 2.0);
-        while (R * (R + 1) / 2 > pr) R--;
-        while ((R + 1) * (R + 2) / 2 <= pr) R++;
-        C = pr - R * (R + 1) / 2;
+        unsigned R, C;  // row-tile R >= column-tile C
+        if (diag_blocks) {  // block b: (2b, 2b), (2b + 1, 2b), (2b + 1, 2b + 1)
+            const unsigned b = pr / 3, j = pr % 3;
+            R = 2 * b + (j > 0 ? 1u : 0u);
+            C = 2 * b + (j == 2 ? 1u : 0u);
+        } else {  // pr = R (R + 1) / 2 + C
+            R = (unsigned)((sqrt(8.0 * pr + 1.0) - 1.0) / 2.0);
+            while (R * (R + 1) / 2 > pr) R--;
+            while ((R + 1) * (R + 2) / 2 <= pr) R++;
+            C = pr - R * (R + 1) / 2;
+        }
         const uint64_t r0 = (uint64_t)R * kDenT, c0 = (uint64_t)C * kDenT;
         float2 acc[4][4];
 #pragma unroll
@@ -247,6 +256,7 @@ static void ens_free(qcw_ensemble *e)
     if (e->psi) cudaFree(e->psi);
     if (e->d_choice) cudaFree(e->d_choice);
     if (e->d_w) cudaFree(e->d_w);
+    if (e->d_err) cudaFree(e->d_err);
     if (e->d_stage) cudaFree(e->d_stage);
     if (e->stream) cudaStreamDestroy(e->stream);
     delete e;
@@ -268,6 +278,7 @@ extern "C" qcw_status qcw_ensemble_create(int nqubits, int nvec, qcw_ensemble **
     if (er == cudaSuccess) er = cudaMalloc(&e->psi, sizeof(float2) * items);
     if (er == cudaSuccess) er = cudaMalloc(&e->d_choice, sizeof(int) * (size_t)nvec);
     if (er == cudaSuccess) er = cudaMalloc(&e->d_w, sizeof(float) * (size_t)nvec);
+    if (er == cudaSuccess) er = cudaMalloc(&e->d_err, sizeof(unsigned));
     if (er == cudaSuccess) er = cudaMalloc(&e->d_stage, sizeof(double2) << nqubits);
     if (er != cudaSuccess) {
         cudaGetLastError();
@@ -397,17 +408,32 @@ extern "C" qcw_status qcw_ensemble_density(qcw_ensemble *e, const double *weight
     qcw_status st = begin_state_replace(ctx);
     if (st) return st;
     const uint64_t dim = 1ull << e->n;
-    if (dim >= (uint64_t)kDenT) {
+    ENS_CK(cudaMemsetAsync(e->d_err, 0, sizeof(unsigned), ctx->stream));
+    if (dim >= 2 * (uint64_t)kDenT && e->n >= 8) {
+        // tiles strictly below the 128 x 128 diagonal blocks on the tensor cores, the diagonal
+        // blocks (trace, probabilities) in FP32
+        const uint64_t blocks = dim / (2 * kDenT), pairs = 3 * blocks;
+        const uint64_t cap = (uint64_t)e->nsm * 8;
+        k_ens_density_tiled<<<(unsigned)(pairs < cap ? pairs : cap), kDenThreads, 0, ctx->stream>>>(
+            e->psi, e->nvec, e->n, e->d_w, ctx->rho, 1);
+        ENS_CK(cudaGetLastError());
+        ctx->launches++;
+        if (!launch_ens_density_tc(e->psi, e->nvec, e->n, e->d_w, ctx->rho, e->d_err, e->nsm, ctx->stream))
+            return set_error(QCW_ECUDA, "tensor-core density kernel could not be configured");
+    } else if (dim >= (uint64_t)kDenT) {
         const uint64_t m = dim / kDenT, pairs = m * (m + 1) / 2;
         const uint64_t cap = (uint64_t)e->nsm * 8;  // 8 CTAs of 256 threads resident per SM
         k_ens_density_tiled<<<(unsigned)(pairs < cap ? pairs : cap), kDenThreads, 0, ctx->stream>>>(
-            e->psi, e->nvec, e->n, e->d_w, ctx->rho);
+            e->psi, e->nvec, e->n, e->d_w, ctx->rho, 0);
     } else {
         k_ens_density<<<ens_grid(dim * dim, e->nsm), kEnsThreads, 0, ctx->stream>>>(e->psi, e->nvec, e->n, e->d_w,
                                                                                    ctx->rho);
     }
     ENS_CK(cudaGetLastError());
     ctx->launches++;
+    unsigned herr = 0;
+    ENS_CK(cudaMemcpyAsync(&herr, e->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
     ENS_CK(cudaStreamSynchronize(ctx->stream));  // the ensemble may change right after
+    if (herr) return set_error(QCW_ETIMEOUT, "ensemble density: a bounded wait ran out");
     return QCW_OK;
 }

@@ -79,6 +79,10 @@ void launch_project(float2 *rho, int n, int qubit, int m, float scale, int nsm, 
 void launch_symmetrize(float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_purity_lower(const float2 *rho, int n, double *partials, double *out, int nblocks, cudaStream_t s);
 void launch_fold(const double *partials, int nblocks, double *out, cudaStream_t s);
+// Multiverse density on the tensor cores (ensemble_tc.cu) for 2^n >= 128: rho = sum_v w_v
+// |psi_v><psi_v|; *err gets bit 0 if a bounded wait ran out.  Returns false if not launched.
+bool launch_ens_density_tc(const float2 *psi, int nvec, int n, const float *w, float2 *rho, unsigned *err, int nsm,
+                           cudaStream_t s);
 void launch_accumulate(float2 *acc, const float2 *x, int n, int nsm, cudaStream_t s);
 // Pauli-string expectations Tr[P rho] (polarisation vectors, spin correlation tensor): per
 // string the row-label masks of its X-or-Y qubits (flipped), Y qubits and Z qubits.

@@ -115,12 +115,13 @@ def test_density_weights_and_validation(q):
     e.close()
 
 
-@pytest.mark.parametrize("n,nvec", [(5, 9), (6, 16), (8, 37), (9, 3)])
+@pytest.mark.parametrize("n,nvec", [(5, 9), (6, 16), (7, 64), (8, 37), (9, 3), (10, 130), (11, 64)])
 def test_density_of_host_vectors_against_the_definition(q, n, nvec):
     """rho = sum_v w_v |psi_v><psi_v| (Eq. rhoE1's ensemble average) of vectors and weights drawn
-    on the host, against the definition in numpy: below 64 amplitudes one thread per element, from
-    64 on the tiled Hermitian kernel (a single diagonal tile at n = 6; lower tiles and their mirrors
-    at n = 8, 9; a partial last round of vectors for nvec = 37)."""
+    on the host, against the definition in numpy: below 64 amplitudes one thread per element, at 64
+    and 128 the tiled FP32 kernel, from 256 on the tensor-core kernel (3xTF32) for the tiles below
+    the 128 x 128 diagonal blocks and their mirrors, the FP32 kernel for the diagonal blocks
+    (partial last rounds of four vectors for nvec = 37, 3 and 130)."""
     rng = np.random.default_rng(64 + n)
     psi = _random_vectors(rng, nvec, n)
     w = rng.uniform(0.1, 1.0, nvec)
