@@ -10,11 +10,11 @@
 // accumulation drops low bits with one sign, which on the diagonal -- sums of positive terms
 // w_v |psi_v[r]|^2 -- moved the trace by 2.6e-6 at 64 vectors, while the off-diagonal elements
 // (either sign) keep FP32-level accuracy.  Per
-// round of four vectors (K = 8) its 128 threads stage A, B1 = [Re B | Im B] and
+// round of eight vectors (two K = 8 slabs of four) its 256 threads stage A, B1 = [Re B | Im B] and
 // B2 = [-Im B | Re B] in shared memory in the no-swizzle K-major layout, each split into a TF32
 // high part and the FP32 remainder (3xTF32: a_hi b_hi + a_lo b_hi + a_hi b_lo, FP32-level
 // accuracy; the remainder keeps either sign, so the MMA's truncation of its low bits has no
-// bias), and one thread issues six MMAs (M = 128, N = 128, K = 8) into two 128-column
+// bias), and one thread issues twelve MMAs (M = 128, N = 128, K = 8) into two 128-column
 // accumulators in tensor memory.  Rounds are double-buffered: the staging of round i + 1
 // overlaps the MMAs of round i, and a buffer is refilled once the MMAs that read it have
 // signalled their mbarrier.  The epilogue reads each thread's row of both accumulators
@@ -26,10 +26,10 @@
 namespace qcw {
 
 constexpr int kEdT = 128;                     // tile edge (MMA M and N)
-constexpr int kEdV = 4;                       // vectors per round: K = 8 (4 real, 4 imaginary parts)
-constexpr int kEdThreads = 128;               // one thread per tile row (tensor-memory lane)
+constexpr int kEdV = 8;                       // vectors per round: two K = 8 slabs of four vectors each
+constexpr int kEdThreads = 256;               // two threads per tile row: one per slab of the round
 constexpr int kEdSlab = kEdT * 8;             // floats of one K = 8 operand slab (128 rows x 32 bytes)
-constexpr int kEdStageFloats = 6 * kEdSlab;   // A_hi, A_lo, B1_hi, B1_lo, B2_hi, B2_lo
+constexpr int kEdStageFloats = 12 * kEdSlab;  // A_hi, A_lo, B1_hi, B1_lo, B2_hi, B2_lo, two slabs each
 constexpr int kEdCols = 256;                  // tensor-memory columns: Re rho (0..127), Im rho (128..255)
 constexpr unsigned kEdWaitLimit = 1u << 20;   // polls (~0.25 s with the 256 ns back-off)
 
@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(kEdThreads) k_ens_density_tc(const float2 *__r
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = *tslot;
-    const unsigned lane_base = ((unsigned)(tid >> 5) * 32u) << 16;
+    const int row = tid & (kEdT - 1), half = tid >> 7;  // tile row (tensor-memory lane) and slab / column half
+    const unsigned lane_base = ((unsigned)((tid >> 5) & 3) * 32u) << 16;
     const uint64_t dim = 1ull << n;
     const unsigned M = (unsigned)(dim / kEdT);
     const unsigned npairs = M * (M - 1) / 2;  // tiles strictly below the diagonal
@@ -104,39 +105,43 @@ __global__ void __launch_bounds__(kEdThreads) k_ens_density_tc(const float2 *__r
                 if (!ok) break;
             }
             float *st = stage + s * kEdStageFloats;
+            // operand o (0 A_hi, 1 A_lo, 2 B1_hi, 3 B1_lo, 4 B2_hi, 5 B2_lo), slab ks at (2 o + ks) slabs
+            auto put = [&](int o, int k, float x) { st[(2 * o + half) * kEdSlab + ed_off(row, k)] = x; };
 #pragma unroll
-            for (int i = 0; i < kEdV; i++) {
-                const int v = rd * kEdV + i;
+            for (int i = 0; i < 4; i++) {  // this thread's slab: vectors 8 rd + 4 half + i
+                const int v = rd * kEdV + 4 * half + i;
                 float2 a = make_float2(0.f, 0.f), b = a;
                 if (v < nvec) {
                     const float2 *pv = psi + ((uint64_t)v << n);
                     const float wv = w[v];
-                    a = pv[r0 + tid];
+                    a = pv[r0 + row];
                     a = make_float2(wv * a.x, wv * a.y);
-                    b = pv[c0 + tid];
+                    b = pv[c0 + row];
                 }
                 float h, l;
-                ed_split(a.x, h, l), st[0 * kEdSlab + ed_off(tid, i)] = h, st[1 * kEdSlab + ed_off(tid, i)] = l;
-                ed_split(a.y, h, l), st[0 * kEdSlab + ed_off(tid, 4 + i)] = h, st[1 * kEdSlab + ed_off(tid, 4 + i)] = l;
-                ed_split(b.x, h, l), st[2 * kEdSlab + ed_off(tid, i)] = h, st[3 * kEdSlab + ed_off(tid, i)] = l;
-                st[4 * kEdSlab + ed_off(tid, 4 + i)] = h, st[5 * kEdSlab + ed_off(tid, 4 + i)] = l;
-                ed_split(b.y, h, l), st[2 * kEdSlab + ed_off(tid, 4 + i)] = h, st[3 * kEdSlab + ed_off(tid, 4 + i)] = l;
-                st[4 * kEdSlab + ed_off(tid, i)] = -h, st[5 * kEdSlab + ed_off(tid, i)] = -l;
+                ed_split(a.x, h, l), put(0, i, h), put(1, i, l);
+                ed_split(a.y, h, l), put(0, 4 + i, h), put(1, 4 + i, l);
+                ed_split(b.x, h, l), put(2, i, h), put(3, i, l), put(4, 4 + i, h), put(5, 4 + i, l);
+                ed_split(b.y, h, l), put(2, 4 + i, h), put(3, 4 + i, l), put(4, i, -h), put(5, i, -l);
             }
             fence_async_smem();  // the generic-proxy writes become visible to the MMAs
             tc_fence_before();
             bar_sync(1, kEdThreads);
             if (tid == 0) {
                 tc_fence_after();
-                const uint64_t ah = tc_sdesc(st + 0 * kEdSlab, 128, 256), al = tc_sdesc(st + 1 * kEdSlab, 128, 256);
-                const uint64_t b1h = tc_sdesc(st + 2 * kEdSlab, 128, 256), b1l = tc_sdesc(st + 3 * kEdSlab, 128, 256);
-                const uint64_t b2h = tc_sdesc(st + 4 * kEdSlab, 128, 256), b2l = tc_sdesc(st + 5 * kEdSlab, 128, 256);
-                tc_mma_tf32_ss(tmem, ah, b1h, idesc, rd > 0);  // Re rho
-                tc_mma_tf32_ss(tmem, al, b1h, idesc, true);
-                tc_mma_tf32_ss(tmem, ah, b1l, idesc, true);
-                tc_mma_tf32_ss(tmem + 128u, ah, b2h, idesc, rd > 0);  // Im rho
-                tc_mma_tf32_ss(tmem + 128u, al, b2h, idesc, true);
-                tc_mma_tf32_ss(tmem + 128u, ah, b2l, idesc, true);
+#pragma unroll
+                for (int ks = 0; ks < 2; ks++) {
+                    auto desc = [&](int o) { return tc_sdesc(st + (2 * o + ks) * kEdSlab, 128, 256); };
+                    const uint64_t ah = desc(0), al = desc(1), b1h = desc(2), b1l = desc(3), b2h = desc(4),
+                                   b2l = desc(5);
+                    const bool acc = rd > 0 || ks > 0;
+                    tc_mma_tf32_ss(tmem, ah, b1h, idesc, acc);  // Re rho
+                    tc_mma_tf32_ss(tmem, al, b1h, idesc, true);
+                    tc_mma_tf32_ss(tmem, ah, b1l, idesc, true);
+                    tc_mma_tf32_ss(tmem + 128u, ah, b2h, idesc, acc);  // Im rho
+                    tc_mma_tf32_ss(tmem + 128u, al, b2h, idesc, true);
+                    tc_mma_tf32_ss(tmem + 128u, ah, b2l, idesc, true);
+                }
                 tc_commit(&bar[s]);
             }
             if (s) cm1++;
@@ -152,21 +157,21 @@ __global__ void __launch_bounds__(kEdThreads) k_ens_density_tc(const float2 *__r
             if (!ok) break;
         }
         tc_fence_after();
-        float2 *row = rho + (r0 + tid) * dim + c0;
-        for (int j0 = 0; j0 < kEdT; j0 += 16) {
+        float2 *rrow = rho + (r0 + row) * dim + c0;
+        for (int j0 = 64 * half; j0 < 64 * half + 64; j0 += 16) {  // this thread's half of the columns
             uint32_t re[16], im[16];
             tmem_ld16(tmem + lane_base + (unsigned)j0, re);
             tmem_ld16(tmem + lane_base + 128u + (unsigned)j0, im);
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 16; j += 2)
-                *reinterpret_cast<float4 *>(row + j0 + j) =
+                *reinterpret_cast<float4 *>(rrow + j0 + j) =
                     make_float4(__uint_as_float(re[j]), __uint_as_float(im[j]), __uint_as_float(re[j + 1]),
                                 __uint_as_float(im[j + 1]));
-            // mirror: rho[c0 + j][r0 + tid] = conj(D[tid][j]); a warp writes 32 consecutive elements
+            // mirror: rho[c0 + j][r0 + row] = conj(D[row][j]); a warp writes 32 consecutive elements
 #pragma unroll
             for (int j = 0; j < 16; j++)
-                rho[(c0 + j0 + j) * dim + r0 + tid] = make_float2(__uint_as_float(re[j]), -__uint_as_float(im[j]));
+                rho[(c0 + j0 + j) * dim + r0 + row] = make_float2(__uint_as_float(re[j]), -__uint_as_float(im[j]));
         }
         tc_fence_before();
         bar_sync(1, kEdThreads);  // every row is read before the next tile's first MMA overwrites it
