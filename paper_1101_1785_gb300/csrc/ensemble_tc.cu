@@ -17,9 +17,10 @@
 // bias), and one thread issues twelve MMAs (M = 128, N = 128, K = 8) into two 128-column
 // accumulators in tensor memory.  Rounds are double-buffered: the staging of round i + 1
 // overlaps the MMAs of round i, and a buffer is refilled once the MMAs that read it have
-// signalled their mbarrier.  The epilogue reads each thread's row of both accumulators
-// (tensor-memory lane = row) and writes the tile and its mirror.  Every wait is bounded; a wait
-// that runs out sets *err and the CTA stops after releasing its tensor memory.
+// signalled their mbarrier.  The epilogue reads each row of both accumulators (tensor-memory
+// lane = row) and writes the tile (through shared memory, as 128-byte runs) and its mirror.
+// Every wait is bounded; a wait that runs out sets *err and the CTA stops after releasing its
+// tensor memory.
 #include "qcw_internal.h"
 #include "tc.cuh"
 
@@ -157,21 +158,30 @@ __global__ void __launch_bounds__(kEdThreads) k_ens_density_tc(const float2 *__r
             if (!ok) break;
         }
         tc_fence_after();
-        float2 *rrow = rho + (r0 + row) * dim + c0;
+        // The stages are free now (every MMA of the tile is done): each half of the threads
+        // passes its 16-column slices of the tile's rows through a padded buffer there, so that the
+        // tile's rows go out as 128-byte runs (16 threads per row) instead of one 16-byte piece per
+        // thread and row.  The mirror is written straight from the registers: for one column j a
+        // warp's 32 rows are 32 consecutive elements of row c0 + j.
+        float2(*buf)[kEdT][17] = reinterpret_cast<float2(*)[kEdT][17]>(stage);  // [half][row][16 + pad]
+        const int hl = tid & (kEdT - 1);  // this thread's index within its half
         for (int j0 = 64 * half; j0 < 64 * half + 64; j0 += 16) {  // this thread's half of the columns
             uint32_t re[16], im[16];
             tmem_ld16(tmem + lane_base + (unsigned)j0, re);
             tmem_ld16(tmem + lane_base + 128u + (unsigned)j0, im);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; j += 2)
-                *reinterpret_cast<float4 *>(rrow + j0 + j) =
-                    make_float4(__uint_as_float(re[j]), __uint_as_float(im[j]), __uint_as_float(re[j + 1]),
-                                __uint_as_float(im[j + 1]));
-            // mirror: rho[c0 + j][r0 + row] = conj(D[row][j]); a warp writes 32 consecutive elements
-#pragma unroll
-            for (int j = 0; j < 16; j++)
+            for (int j = 0; j < 16; j++) {
+                buf[half][row][j] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
                 rho[(c0 + j0 + j) * dim + r0 + row] = make_float2(__uint_as_float(re[j]), -__uint_as_float(im[j]));
+            }
+            bar_sync(1, kEdThreads);
+#pragma unroll 4
+            for (int i = 0; i < 16; i++) {  // element e = hl + 128 i of the half's 128 x 16 slice
+                const int e = hl + kEdT * i, r = e >> 4, jj = e & 15;
+                rho[(r0 + r) * dim + c0 + j0 + jj] = buf[half][r][jj];
+            }
+            bar_sync(1, kEdThreads);  // the slice is out before the next one overwrites the buffer
         }
         tc_fence_before();
         bar_sync(1, kEdThreads);  // every row is read before the next tile's first MMA overwrites it
