@@ -12,6 +12,9 @@
 // and scatters them back.  Groups of one phase are disjoint, so phases need no atomics.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "planner.h"
 #include "qcw_internal.h"
@@ -69,7 +72,8 @@ struct CachedPlan {
 
 // Measured choice of the fusion width (fuse_k = 0).  Segments of at least kTuneMinOps
 // operations are timed with events at a candidate width until a choice is made, then the
-// choice holds for the context's lifetime.  Segments differ too much in content for one trial
+// choice holds for the context's lifetime and for later contexts of the same device, register
+// size and kernel choice (g_tuned).  Segments differ too much in content for one trial
 // per width to decide, so a segment that comes back (same operations, recognised by hash, as
 // in a circuit replayed step after step) is run at the other width: after kTunePairs such
 // pairs the width with the smaller summed time wins.  Without repeats the widths alternate
@@ -88,6 +92,7 @@ struct KTuneSeg {
 
 struct KTune {
     int chosen = 0;          // 0 until decided
+    bool recorded = false;   // the choice is in the process-wide table
     int trials = 0;          // trials finished
     double ms[2] = {0, 0};   // per candidate: summed trial time
     double ops[2] = {0, 0};  // and summed operations
@@ -112,6 +117,25 @@ struct FusedRuntime {
     std::vector<cudaEvent_t> ev_free, ev_pending;  // pairs: start, stop
     KTune tune;
 };
+
+// A width once chosen by measurement holds for every context of the same device, register size
+// and kernel choice in the process: later contexts start with it and run no trials (a second
+// context's trials, timed while other work shares the GPU, could otherwise pick differently).
+static std::mutex g_tuned_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned;
+
+static int tuned_width(const qcw_ctx *c)
+{
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto it = g_tuned.find(std::make_tuple(c->dev, c->n, c->fused_kernel));
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
+static void record_width(const qcw_ctx *c, int k)
+{
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    g_tuned.emplace(std::make_tuple(c->dev, c->n, c->fused_kernel), k);
+}
 
 // Collect the pending trial, waiting for it: until the choice is made the host keeps pace with
 // the timed segments (otherwise, with readouts that do not synchronise, the host would run
@@ -809,6 +833,7 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e, bool last)
     KTune &tn = rt->tune;
     bool trial = false;
     int k;
+    if (!c->fuse_k && !tn.chosen) tn.chosen = tuned_width(c);
     if (c->fuse_k) {
         k = c->fuse_k;
     } else if (tn.chosen) {
@@ -831,6 +856,10 @@ static qcw_status run_segment(qcw_ctx *c, size_t b, size_t e, bool last)
         trial = true;
     } else {
         k = tn.chosen ? tn.chosen : auto_k(c->queue, b, e, n, herm0, herm0 ? 12 : 13);
+    }
+    if (tn.chosen && !tn.recorded) {
+        record_width(c, tn.chosen);
+        tn.recorded = true;
     }
     if (k > n) k = n;
     const bool herm = herm0;
