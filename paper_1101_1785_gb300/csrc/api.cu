@@ -199,9 +199,44 @@ static void quartet_layout(int n, int q1, int q2, int *pos, uint64_t *offr, uint
     }
 }
 
+// One entry per row, at a distinct column, each exactly 1, -1, i or -i: sigma[i] = its column.
+static bool monomial4(const c128 *u, int *sigma, c128 *val)
+{
+    bool used[4] = {false, false, false, false};
+    for (int i = 0; i < 4; i++) {
+        sigma[i] = -1;
+        for (int j = 0; j < 4; j++) {
+            const c128 z = u[4 * i + j];
+            if (z == c128(0, 0)) continue;
+            const bool unit = z == c128(1, 0) || z == c128(-1, 0) || z == c128(0, 1) || z == c128(0, -1);
+            if (!unit || sigma[i] >= 0 || used[j]) return false;
+            sigma[i] = j;
+            val[i] = z;
+            used[j] = true;
+        }
+        if (sigma[i] < 0) return false;
+    }
+    return true;
+}
+
 qcw_status plain_gate2(qcw_ctx *c, const c128 *u, int q1, int q2, const int *ctrl, int nc)
 {
     const int n = c->n;
+    int sigma[4];
+    c128 val[4];
+    if (nc == 0 && monomial4(u, sigma, val)) {  // CNOT, CZ, SWAP, ...: an exact permutation
+        Mono2Params p{};
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++) p.ph[4 * i + j] = f2(val[i] * std::conj(val[j]));
+        quartet_layout(n, q1, q2, p.pos, p.off_r, p.off_c);
+        for (int i = 0; i < 4; i++) {
+            p.src_r[i] = p.off_r[sigma[i]];
+            p.src_c[i] = p.off_c[sigma[i]];
+        }
+        launch_mono2(p, c->rho, n, c->nsm, c->stream);
+        CKLAUNCH(c, 1);
+        return QCW_OK;
+    }
     if (nc == 0) {
         const int qs[2] = {q1, q2};
         return plain_super(c, gate_superop(u, 2), qs, 2);

@@ -286,6 +286,41 @@ void launch_super2(const Super2Params &p, float2 *rho, int n, int nsm, cudaStrea
     }
 }
 
+// --------------------------------------------------------------------- monomial two-qubit gates
+// A gate with one entry u_i of modulus 1 per row, at column sigma(i), and entries among
+// 1, -1, i, -i (CNOT, CZ, SWAP, iSWAP): (U rho U^dagger)_ij = u_i conj(u_j) rho_sigma(i)sigma(j),
+// a permutation of each 16-member group with exact sign / quarter-turn factors -- a pure data
+// movement (no rounding at all, so the trace is kept exactly), one read and one write of rho.
+template <int V>
+__global__ void k_mono2(float2 *__restrict__ rho, uint64_t nitems, Mono2Params p)
+{
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < nitems;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t g = group_base(V * s, p.pos);
+        float2 x[V][16];
+        load16<V>(rho, g, p.src_r, p.src_c, x);  // x[4 i + j] = the input member (sigma(i), sigma(j))
+#pragma unroll
+        for (int v = 0; v < V; v++)
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                const float2 a = x[v][e], f = p.ph[e];
+                x[v][e] = make_float2(f.x * a.x - f.y * a.y, f.x * a.y + f.y * a.x);
+            }
+        store16<V>(rho, g, p.off_r, p.off_c, x);
+    }
+}
+
+void launch_mono2(const Mono2Params &p, float2 *rho, int n, int nsm, cudaStream_t s)
+{
+    uint64_t ng = 1ull << (2 * n - 4);
+    const int th = 128;
+    if (p.pos[0] == 0) {
+        k_mono2<1><<<grid_for(ng, th, nsm), th, 0, s>>>(rho, ng, p);
+    } else {
+        k_mono2<2><<<grid_for(ng / 2, th, nsm), th, 0, s>>>(rho, ng / 2, p);
+    }
+}
+
 // --------------------------------------------------------------------- one-qubit channel
 // Superoperator S = sum_k K (x) conj(K) (Eq. rhoE2; a gate is S = U (x) conj U) on the quartet
 // (x00, x01, x10, x11), e = 2*row+col, in the Pauli basis of the qubit: (I, X, D, Z) =

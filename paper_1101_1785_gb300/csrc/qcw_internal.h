@@ -45,6 +45,13 @@ struct Super2Params {
     uint64_t off_r[4], off_c[4];
 };
 
+struct Mono2Params {   // uncontrolled two-qubit gate with one entry of modulus 1 per row (CNOT, CZ, SWAP, ...)
+    float2 ph[16];     // member e = 4 i + j of the output: u_i conj(u_j) (one of 1, -1, i, -i, exact)
+    int pos[4];        //   times the input member (sigma(i), sigma(j))
+    uint64_t off_r[4], off_c[4];    // offsets of the output members
+    uint64_t src_r[4], src_c[4];    // offsets of their inputs: off_r[sigma(i)], off_c[sigma(j)]
+};
+
 struct GateKParams {   // one side (rows or columns) of a k-qubit dense gate, k <= 5
     float2 u[1024];    // U (or conj(U) for the column side), 2^k x 2^k row-major
     int k;
@@ -63,6 +70,7 @@ void launch_gate1(const Gate1Params &p, float2 *rho, int n, int nsm, cudaStream_
 void launch_gate2(const Gate2Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_super1(const Super1Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_super2(const Super2Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_mono2(const Mono2Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_gatek_side(const GateKParams &p, float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_zero_state(float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_c128_to_c64(const double2 *src, float2 *dst, size_t count, int nsm, cudaStream_t s);

@@ -372,3 +372,40 @@ def test_validation_mode(q):
         d.set_validation(False)
         d.reset()
     d.close()
+
+
+def test_monomial_two_qubit_gates_are_exact_permutations(q):
+    """CNOT (both orders), CZ, SWAP, iSWAP and Pauli products on the plain path move the members
+    of each 16-element group with factors 1, -1, i, -i only: the result equals the oracle and
+    every element is a signed / rotated copy of an input element, so the trace (a permutation of
+    the diagonal) is unchanged to the last bit; a gate that is not of that form (a Haar unitary)
+    and a controlled monomial take the general kernels and still match the oracle."""
+    n = 5
+    rng = np.random.default_rng(92)
+    rho = random_rho(rng, n)
+    d = q.Density(n)
+    d.set_state(rho)
+    want = rho.copy()
+    iswap = np.array([[1, 0, 0, 0], [0, 0, 1j, 0], [0, 1j, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+    xz = np.kron(wl.gate_matrix("X"), wl.gate_matrix("Z"))
+    yy = np.kron(wl.gate_matrix("Y"), wl.gate_matrix("Y"))
+    gates = [(wl.gate_matrix("CNOT"), (0, 4)), (wl.gate_matrix("CNOT"), (4, 0)), (wl.gate_matrix("CZ"), (1, 3)),
+             (wl.gate_matrix("SWAP"), (2, 4)), (iswap, (3, 0)), (xz, (1, 2)), (yy, (4, 3))]
+    tr0 = d.trace()
+    for u, (a, b) in gates:
+        d.apply_gate2(u, a, b)
+        oracle.apply_unitary(want, u, [a, b])
+        assert d.trace() == tr0
+    got = d.get_state()
+    assert np.abs(got - want).max() <= 1e-6
+    vals = np.sort(np.abs(np.concatenate([got.real.ravel(), got.imag.ravel()])))
+    src = np.sort(np.abs(np.concatenate([d_ for d_ in (rho.astype(np.complex64).real.ravel(),
+                                                          rho.astype(np.complex64).imag.ravel())])))
+    np.testing.assert_array_equal(vals.astype(np.float32), src.astype(np.float32))
+    u = haar_unitary(rng, 4)
+    d.apply_gate2(u, 0, 2)
+    oracle.apply_unitary(want, u, [0, 2])
+    d.apply_gate2(wl.gate_matrix("CNOT"), 1, 3, [4])
+    oracle.apply_unitary(want, wl.gate_matrix("CNOT"), [1, 3], [4])
+    assert np.abs(d.get_state() - want).max() <= 1e-5
+    d.close()
