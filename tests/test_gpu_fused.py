@@ -2,7 +2,8 @@
 
 Tolerance as everywhere: max |delta rho| <= 1e-5, |tr rho - 1| <= 1e-6 (FP32 state vs the
 FP64 oracle).  The 14-qubit cases run in the launch configuration the benchmark times
-(fusion width 5, 2^13-element tiles).
+(fusion width 5, 2^12-element Hermitian tiles); the 17-qubit cases run at the largest
+register the library takes (QCW_MAX_QUBITS, rho = 128 GiB).
 """
 
 import numpy as np
@@ -161,6 +162,83 @@ def test_full_size_n14_embedded_subsystem(q):
     assert np.abs(block - want_s).max() <= ATOL
     t[idx] = 0
     assert np.abs(got).max() == 0.0
+
+
+def _embedded_index(n, S):
+    """Row (or column) indices of rho whose bits outside the qubits S are 0, in the order of the
+    subsystem's own index (qubit 0 the most significant bit, as everywhere)."""
+    out = np.zeros(1 << len(S), dtype=np.int64)
+    for s in range(1 << len(S)):
+        for j, qb in enumerate(S):
+            if (s >> (len(S) - 1 - j)) & 1:
+                out[s] |= 1 << (n - 1 - qb)
+    return out
+
+
+def _gather(d, rows, cols):
+    """Elements (rows[i], cols[i]) of the context's rho, gathered on the device (the state is
+    completed and ordered on the context's stream before its pointer is returned)."""
+    import torch
+
+    ptr, sp = d.device_state()
+    torch.cuda.ExternalStream(sp).synchronize()
+    dim = 1 << d.n
+
+    class _Buf:
+        pass
+
+    buf = _Buf()
+    buf.__cuda_array_interface__ = {"shape": (dim, 2 * dim), "typestr": "<f4", "data": (ptr, False), "version": 2}
+    view = torch.as_tensor(buf, device="cuda")
+    r = torch.as_tensor(np.asarray(rows, dtype=np.int64), device="cuda")
+    c2 = torch.as_tensor(2 * np.asarray(cols, dtype=np.int64), device="cuda")
+    return view[r, c2].double().cpu().numpy() + 1j * view[r, c2 + 1].double().cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+def test_max_size_n17_embedded_subsystem(q, mode):
+    """The largest register, 17 qubits (rho = 2^34 complex64 = 128 GiB: element offsets beyond
+    32 bits in every kernel on the path), on a noisy circuit confined to five qubits spread over
+    the register: the 32 x 32 block rho_S against the oracle, seeded elements outside it exactly
+    0, and the trace, purity and per-qubit probabilities."""
+    import torch
+
+    from paper_1101_1785_gb300._binding import QCW_MAX_QUBITS
+
+    n = QCW_MAX_QUBITS
+    free, _ = torch.cuda.mem_get_info()
+    if free < (8 << (2 * n)) + (16 << 30):
+        pytest.skip(f"needs {(8 << (2 * n)) >> 30} GiB of free device memory and some headroom")
+    S = [0, 5, 9, 14, 16]
+    small = wl.random_circuit(5, 120 if mode == "fused" else 30, 1717, "mixed", "adpd")
+    want_s = oracle.run_circuit(small)
+    d = q.Density(n)
+    if mode == "fused":
+        d.set_mode(q.QCW_MODE_FUSED, 5)
+    for op in small.ops:
+        mapped = [S[x] for x in op.qubits]
+        if op.kind == "gate":
+            if op.k == 1:
+                d.apply_gate1(op.mats[0], mapped[0])
+            else:
+                d.apply_gate2(op.mats[0], mapped[0], mapped[1])
+        else:
+            d.apply_kraus(op.mats, mapped)
+    idx = _embedded_index(n, S)
+    rr, cc = np.meshgrid(idx, idx, indexing="ij")
+    block = _gather(d, rr.ravel(), cc.ravel()).reshape(32, 32)
+    assert np.abs(block - want_s).max() <= ATOL
+    rng = np.random.default_rng(17)
+    rows = rng.integers(0, 1 << n, 8192)
+    cols = rng.integers(0, 1 << n, 8192)
+    outside = ~(np.isin(rows, idx) & np.isin(cols, idx))
+    assert np.all(_gather(d, rows[outside], cols[outside]) == 0)
+    assert abs(d.trace() - 1) <= TRACE_TOL
+    assert abs(d.purity() - oracle.purity(want_s)) <= 2 * TRACE_TOL
+    p = d.probabilities()
+    np.testing.assert_allclose(p[S], oracle.probabilities(want_s), atol=1e-6)
+    assert np.all(np.delete(p, S) == 0)
+    d.close()
 
 
 def test_full_size_n14_config3_prefix(q):
