@@ -17,7 +17,8 @@
 // bias), and one thread issues twelve MMAs (M = 128, N = 128, K = 8) into two 128-column
 // accumulators in tensor memory.  Rounds are double-buffered: the staging of round i + 1
 // overlaps the MMAs of round i, and a buffer is refilled once the MMAs that read it have
-// signalled their mbarrier.  The epilogue reads each row of both accumulators (tensor-memory
+// signalled their mbarrier; each thread loads its amplitudes one round ahead and writes its
+// row of every operand slab as 16-byte pieces.  The epilogue reads each row of both accumulators (tensor-memory
 // lane = row) and writes the tile (through shared memory, as 128-byte runs) and its mirror.
 // Every wait is bounded; a wait that runs out sets *err and the CTA stops after releasing its
 // tensor memory.
@@ -97,7 +98,31 @@ __global__ void __launch_bounds__(kEdThreads) k_ens_density_tc(const float2 *__r
         while ((R + 1) * R / 2 <= pr) R++;
         const unsigned C = pr - R * (R - 1) / 2;
         const uint64_t r0 = (uint64_t)R * kEdT, c0 = (uint64_t)C * kEdT;
+        // This thread's amplitudes of a round (its slab: vectors 8 rd + 4 half + i), loaded one
+        // round ahead so that their latency overlaps the previous round's staging and MMAs.
+        float2 na[4], nb[4];
+        float nw[4];
+        auto fetch = [&](int rd) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int v = rd * kEdV + 4 * half + i;
+                na[i] = nb[i] = make_float2(0.f, 0.f);
+                nw[i] = 0.f;
+                if (v < nvec) {
+                    const float2 *pv = psi + ((uint64_t)v << n);
+                    nw[i] = w[v];
+                    na[i] = pv[r0 + row];
+                    nb[i] = pv[c0 + row];
+                }
+            }
+        };
+        fetch(0);
         for (int rd = 0; rd < nround; rd++) {
+            float2 ca[4], cb[4];
+            float cw[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) ca[i] = na[i], cb[i] = nb[i], cw[i] = nw[i];
+            if (rd + 1 < nround) fetch(rd + 1);
             const int s = rd & 1;
             const unsigned cms = s ? cm1 : cm0;
             if (cms > 0) {  // the MMAs that last read stage s are done before it is refilled
@@ -106,25 +131,25 @@ __global__ void __launch_bounds__(kEdThreads) k_ens_density_tc(const float2 *__r
                 if (!ok) break;
             }
             float *st = stage + s * kEdStageFloats;
-            // operand o (0 A_hi, 1 A_lo, 2 B1_hi, 3 B1_lo, 4 B2_hi, 5 B2_lo), slab ks at (2 o + ks) slabs
-            auto put = [&](int o, int k, float x) { st[(2 * o + half) * kEdSlab + ed_off(row, k)] = x; };
+            // operand o (0 A_hi, 1 A_lo, 2 B1_hi, 3 B1_lo, 4 B2_hi, 5 B2_lo), slab ks at (2 o + ks)
+            // slabs; this thread's row of its slab: K index k = i (real parts, or -Im for B2) and
+            // 4 + i (imaginary parts, or Re for B2), written as two 16-byte pieces per operand
+            float op[6][8];
 #pragma unroll
-            for (int i = 0; i < 4; i++) {  // this thread's slab: vectors 8 rd + 4 half + i
-                const int v = rd * kEdV + 4 * half + i;
-                float2 a = make_float2(0.f, 0.f), b = a;
-                if (v < nvec) {
-                    const float2 *pv = psi + ((uint64_t)v << n);
-                    const float wv = w[v];
-                    a = pv[r0 + row];
-                    a = make_float2(wv * a.x, wv * a.y);
-                    b = pv[c0 + row];
-                }
+            for (int i = 0; i < 4; i++) {
+                const float2 a = make_float2(cw[i] * ca[i].x, cw[i] * ca[i].y), b = cb[i];
                 float h, l;
-                ed_split(a.x, h, l), put(0, i, h), put(1, i, l);
-                ed_split(a.y, h, l), put(0, 4 + i, h), put(1, 4 + i, l);
-                ed_split(b.x, h, l), put(2, i, h), put(3, i, l), put(4, 4 + i, h), put(5, 4 + i, l);
-                ed_split(b.y, h, l), put(2, 4 + i, h), put(3, 4 + i, l), put(4, i, -h), put(5, i, -l);
+                ed_split(a.x, op[0][i], op[1][i]);
+                ed_split(a.y, op[0][4 + i], op[1][4 + i]);
+                ed_split(b.x, h, l), op[2][i] = h, op[3][i] = l, op[4][4 + i] = h, op[5][4 + i] = l;
+                ed_split(b.y, h, l), op[2][4 + i] = h, op[3][4 + i] = l, op[4][i] = -h, op[5][i] = -l;
             }
+#pragma unroll
+            for (int o = 0; o < 6; o++)
+#pragma unroll
+                for (int kh = 0; kh < 2; kh++)
+                    *reinterpret_cast<float4 *>(st + (2 * o + half) * kEdSlab + ed_off(row, 4 * kh)) =
+                        make_float4(op[o][4 * kh], op[o][4 * kh + 1], op[o][4 * kh + 2], op[o][4 * kh + 3]);
             fence_async_smem();  // the generic-proxy writes become visible to the MMAs
             tc_fence_before();
             bar_sync(1, kEdThreads);
