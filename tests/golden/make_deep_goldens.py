@@ -22,6 +22,9 @@ What is recorded, in the order the benchmark reads it:
     over (0, 1) and the purity of the renormalised post-measurement state.
 
 ``--state-dir`` keeps the oracle state every 100 gates so that an interrupted run resumes.
+The 14-qubit state is 4 GiB of complex128: run with ``GLIBC_TUNABLES=glibc.malloc.hugetlb=1``
+(transparent huge pages for large allocations), else page faults take most of the host time
+(about three hours on 8 cores with them).
 """
 
 from __future__ import annotations
