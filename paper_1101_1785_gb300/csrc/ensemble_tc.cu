@@ -18,8 +18,9 @@
 // accumulators in tensor memory.  Rounds are double-buffered: the staging of round i + 1
 // overlaps the MMAs of round i, and a buffer is refilled once the MMAs that read it have
 // signalled their mbarrier; each thread loads its amplitudes one round ahead and writes its
-// row of every operand slab as 16-byte pieces.  The epilogue reads each row of both accumulators (tensor-memory
-// lane = row) and writes the tile (through shared memory, as 128-byte runs) and its mirror.
+// row of every operand slab as 16-byte pieces.  The epilogue reads each row of both
+// accumulators (tensor-memory lane = row) and writes the tile (through shared memory, as
+// 128-byte runs) and its mirror.
 // Every wait is bounded; a wait that runs out sets *err and the CTA stops after releasing its
 // tensor memory.
 #include "qcw_internal.h"
