@@ -104,3 +104,24 @@ def numpy_partial_trace(rho: np.ndarray, keep, n: int) -> np.ndarray:
     res = np.einsum("".join(rin) + "".join(cin) + "->" + out, t)
     da = 1 << len(keep)
     return res.reshape(da, da)
+
+
+def gather_elements(d, rows, cols) -> np.ndarray:
+    """Elements (rows[i], cols[i]) of a qcw Density's rho, gathered on the device and returned as
+    complex128 (the library completes the state and orders it on the context's stream before it
+    hands out the pointer).  Reads a few elements of a state too large to copy to the host."""
+    import torch
+
+    ptr, sp = d.device_state()
+    torch.cuda.ExternalStream(sp).synchronize()
+    dim = 1 << d.n
+
+    class _Buf:
+        pass
+
+    buf = _Buf()
+    buf.__cuda_array_interface__ = {"shape": (dim, 2 * dim), "typestr": "<f4", "data": (ptr, False), "version": 2}
+    view = torch.as_tensor(buf, device="cuda")
+    r = torch.as_tensor(np.asarray(rows, dtype=np.int64), device="cuda")
+    c2 = torch.as_tensor(2 * np.asarray(cols, dtype=np.int64), device="cuda")
+    return view[r, c2].double().cpu().numpy() + 1j * view[r, c2 + 1].double().cpu().numpy()

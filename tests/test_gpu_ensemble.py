@@ -137,3 +137,40 @@ def test_density_of_host_vectors_against_the_definition(q, n, nvec):
     assert abs(d.trace() - 1) <= 1e-6
     d.close()
     e.close()
+
+
+def test_density_at_the_largest_register(q):
+    """17 qubits (rho = 2^34 complex64 = 128 GiB, element offsets beyond 32 bits): rho = sum_v w_v
+    |psi_v><psi_v| of 16 vectors drawn on the host, at seeded elements on, below and above the
+    diagonal, against the definition (within 1e-5 of the largest element; the amplitudes are FP32
+    on the device), Hermitian at the mirrored positions, trace 1."""
+    import torch
+
+    from paper_1101_1785_gb300._binding import QCW_MAX_QUBITS
+    from tests._helpers import gather_elements
+
+    n, nvec = QCW_MAX_QUBITS, 16
+    free, _ = torch.cuda.mem_get_info()
+    if free < (8 << (2 * n)) + (16 << 30):
+        pytest.skip(f"needs {(8 << (2 * n)) >> 30} GiB of free device memory and some headroom")
+    rng = np.random.default_rng(1717)
+    psi = _random_vectors(rng, nvec, n)
+    w = rng.uniform(0.1, 1.0, nvec)
+    w /= w.sum()
+    e = q.Ensemble(n, nvec)
+    e.set(psi)
+    d = q.Density(n)
+    e.density(w, d)
+    dim = 1 << n
+    diag = rng.integers(0, dim, 512)
+    rows = np.concatenate([diag, rng.integers(0, dim, 4096)])
+    cols = np.concatenate([diag, rng.integers(0, dim, 4096)])
+    want = np.einsum("v,vi,vi->i", w, psi[:, rows], psi[:, cols].conj())
+    got = gather_elements(d, rows, cols)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+    # off the 64 x 64 diagonal tiles each mirror is written as the exact conjugate; inside them
+    # (the sampled diagonal) both triangles are computed, equal to rounding
+    assert np.abs(gather_elements(d, cols, rows) - got.conj()).max() <= 1e-5 * np.abs(want).max()
+    assert abs(d.trace() - 1) <= 1e-6
+    d.close()
+    e.close()

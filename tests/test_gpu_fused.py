@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from tests._helpers import haar_unitary, random_rho
+from tests._helpers import gather_elements, haar_unitary, random_rho
 
 pytestmark = pytest.mark.gpu
 
@@ -175,26 +175,6 @@ def _embedded_index(n, S):
     return out
 
 
-def _gather(d, rows, cols):
-    """Elements (rows[i], cols[i]) of the context's rho, gathered on the device (the state is
-    completed and ordered on the context's stream before its pointer is returned)."""
-    import torch
-
-    ptr, sp = d.device_state()
-    torch.cuda.ExternalStream(sp).synchronize()
-    dim = 1 << d.n
-
-    class _Buf:
-        pass
-
-    buf = _Buf()
-    buf.__cuda_array_interface__ = {"shape": (dim, 2 * dim), "typestr": "<f4", "data": (ptr, False), "version": 2}
-    view = torch.as_tensor(buf, device="cuda")
-    r = torch.as_tensor(np.asarray(rows, dtype=np.int64), device="cuda")
-    c2 = torch.as_tensor(2 * np.asarray(cols, dtype=np.int64), device="cuda")
-    return view[r, c2].double().cpu().numpy() + 1j * view[r, c2 + 1].double().cpu().numpy()
-
-
 @pytest.mark.parametrize("mode", ["fused", "plain"])
 def test_max_size_n17_embedded_subsystem(q, mode):
     """The largest register, 17 qubits (rho = 2^34 complex64 = 128 GiB: element offsets beyond
@@ -226,13 +206,13 @@ def test_max_size_n17_embedded_subsystem(q, mode):
             d.apply_kraus(op.mats, mapped)
     idx = _embedded_index(n, S)
     rr, cc = np.meshgrid(idx, idx, indexing="ij")
-    block = _gather(d, rr.ravel(), cc.ravel()).reshape(32, 32)
+    block = gather_elements(d, rr.ravel(), cc.ravel()).reshape(32, 32)
     assert np.abs(block - want_s).max() <= ATOL
     rng = np.random.default_rng(17)
     rows = rng.integers(0, 1 << n, 8192)
     cols = rng.integers(0, 1 << n, 8192)
     outside = ~(np.isin(rows, idx) & np.isin(cols, idx))
-    assert np.all(_gather(d, rows[outside], cols[outside]) == 0)
+    assert np.all(gather_elements(d, rows[outside], cols[outside]) == 0)
     assert abs(d.trace() - 1) <= TRACE_TOL
     assert abs(d.purity() - oracle.purity(want_s)) <= 2 * TRACE_TOL
     p = d.probabilities()
