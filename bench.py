@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--impl", default="qcw", choices=["qcw", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-gates", type=int, default=3, help="gates of the timed oracle sample (all cores)")
+    ap.add_argument("--cpu-baseline-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the untimed accuracy leg and the plain / batch / serve sub-measurements")
     ap.add_argument("--workload", default="circuit14", choices=["circuit14", "plain12", "batch", "serve", "ensemble"],
@@ -255,6 +256,17 @@ def oracle_timed(ngates: int, steps: int = 1, warmup: int = 0, one_core: bool = 
         oracle.set_threads(nthreads)
     del rho
     return times, used, one
+
+
+def cpu_baseline_subprocess(ngates: int):
+    """cpu_baseline_legs in a fresh interpreter that never touches the GPU -- the environment the
+    reference arm times the oracle in (inside the process that holds the CUDA context the same
+    sample ran about a quarter slower)."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-leg", "--cpu-gates", str(ngates)],
+                       capture_output=True, text=True, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(f"CPU-baseline leg failed:\n{r.stdout[-2000:]}\n{r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def cpu_baseline_legs(ngates: int):
@@ -481,7 +493,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and nq == N_QUBITS:
-        cpu = cpu_baseline_legs(args.cpu_gates)
+        cpu = cpu_baseline_subprocess(args.cpu_gates)
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         import paper_1101_1785_gb300 as q2
@@ -789,7 +801,9 @@ def _standalone(args, what):
 
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.cpu_baseline_leg:
+        print(json.dumps(cpu_baseline_legs(args.cpu_gates)), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload in ("plain12", "batch", "serve", "ensemble"):
         _standalone(args, args.workload)
