@@ -242,11 +242,12 @@ def test_torch_owned_memory_and_stream(q, mode, kernel, k):
     del t, backing, snap
 
 
-@pytest.mark.parametrize("mode,kernel,k", [("fused", 0, 0), ("fused", 4, 5)])
+@pytest.mark.parametrize("mode,kernel,k", [("fused", 0, 0), ("fused", 4, 5), ("plain", 0, 0)])
 def test_benchmark_circuit_full_depth_n14_against_stored_oracle(q, mode, kernel, k):
     """The 14-qubit benchmark circuit itself, all 1000 gates, in the benchmark's launch
-    configuration (the default kernel at the autotuned width, and the tensor-core variant),
-    against the complex128 oracle's readouts stored by tests/golden/make_deep_goldens.py: every
+    configuration (the default kernel at the autotuned width), on the tensor-core variant and on
+    the plain path (one launch per gate and per channel, 3296 launches), against the complex128
+    oracle's readouts stored by tests/golden/make_deep_goldens.py: every
     100-gate checkpoint (trace, purity, probabilities), 1024 sampled elements of the final state,
     two partial traces, the u-driven measurement of qubit 0 and the post-measurement state."""
     import os
@@ -260,8 +261,9 @@ def test_benchmark_circuit_full_depth_n14_against_stored_oracle(q, mode, kernel,
     assert g["n"] == [c.n] and g["gates"] == [c.n_gates] and g["channels"] == [c.n_channels]
     ck_want = [row for key, row in read_golden("config3_n14.txt") if key == "ckpt"]
     d = q.Density(c.n)
-    d.set_mode(q.QCW_MODE_FUSED, k)
-    d.set_fused_kernel(kernel)
+    if mode == "fused":
+        d.set_mode(q.QCW_MODE_FUSED, k)
+        d.set_fused_kernel(kernel)
     ck = _bench_like(q, d, c)
     assert len(ck) == len(ck_want) == 10
     for (gtr, gpu, gpr), w in zip(ck, ck_want):
