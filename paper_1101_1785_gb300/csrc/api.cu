@@ -319,8 +319,9 @@ qcw_status plain_super(qcw_ctx *c, const std::vector<c128> &s, const int *qs, in
 }
 
 // Half storage: the warp-specialised pass keeps only the lower triangle current; everything
-// that reads the other triangle (plain kernels, the other fused kernels, state downloads, the
-// partial trace, direct device access) completes the matrix first.
+// that reads the other triangle (plain kernels, the other fused kernels, state downloads, direct
+// device access) completes the matrix first.  The readouts (trace, probabilities, purity, Pauli
+// expectations, partial trace) and the measurement projection work on the lower triangle as it is.
 qcw_status ensure_full(qcw_ctx *c)
 {
     if (!c->half) return QCW_OK;
@@ -1060,7 +1061,7 @@ extern "C" qcw_status qcw_measure(qcw_ctx *ctx, int qubit, int forced, double u,
     if (prob) *prob = pm;
     if (!(pm >= 1e-12)) return set_error(QCW_EZEROPROB, "outcome probability below 1e-12");
     ctx->state_ver++;
-    launch_project(ctx->rho, ctx->n, qubit, m, (float)(1.0 / pm), ctx->nsm, ctx->stream);
+    launch_project(ctx->rho, ctx->n, qubit, m, (float)(1.0 / pm), ctx->half, ctx->nsm, ctx->stream);
     CKLAUNCH(ctx, 1);
     return QCW_OK;
 }
@@ -1075,11 +1076,11 @@ extern "C" qcw_status qcw_partial_trace(qcw_ctx *ctx, const int *keep, int nkeep
         if (j && keep[j] <= keep[j - 1]) return set_error(QCW_EINVAL, "kept qubits must ascend");
     }
     qcw_status st = fused_flush(ctx);
-    if (!st) st = ensure_full(ctx);
     if (st) return st;
     PTParams p{};
     p.n = n;
     p.nkeep = nkeep;
+    p.lower = ctx->half ? 1 : 0;  // half storage is read as it is: no completion pass
     unsigned kept = 0;
     for (int j = 0; j < nkeep; j++) {
         p.kpos[j] = (int8_t)(n - 1 - keep[j]);

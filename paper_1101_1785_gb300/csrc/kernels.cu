@@ -753,12 +753,16 @@ void launch_symmetrize(float2 *rho, int n, int nsm, cudaStream_t s)
 }
 
 // Projector and renormalisation: keep (r, c) with qubit bit == m on both sides, times scale;
-// every other element becomes 0 (read only when kept).
-__global__ void k_project(float4 *__restrict__ rho4, uint64_t npairs, int pc, int pr, int m, float scale)
+// every other element becomes 0 (read only when kept).  lower (half storage: only r >= c is
+// current): element pairs wholly above the diagonal are left alone (n is the register size).
+__global__ void k_project(float4 *__restrict__ rho4, uint64_t npairs, int pc, int pr, int m, float scale, int n,
+                          int lower)
 {
+    const uint64_t cmask = (1ull << n) - 1;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < npairs;
          t += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t g = 2 * t;
+        if (lower && (g & cmask) > (g >> n)) continue;
         bool rk = (int)((g >> pr) & 1) == m;
         bool k0 = rk && (int)((g >> pc) & 1) == m;
         bool k1 = rk && (int)(((g + 1) >> pc) & 1) == m;
@@ -772,11 +776,23 @@ __global__ void k_project(float4 *__restrict__ rho4, uint64_t npairs, int pc, in
     }
 }
 
-void launch_project(float2 *rho, int n, int qubit, int m, float scale, int nsm, cudaStream_t s)
+void launch_project(float2 *rho, int n, int qubit, int m, float scale, bool lower, int nsm, cudaStream_t s)
 {
     uint64_t npairs = (1ull << (2 * n)) / 2;
     int pc = n - 1 - qubit, pr = 2 * n - 1 - qubit;
-    k_project<<<grid_for(npairs, 256, nsm), 256, 0, s>>>(reinterpret_cast<float4 *>(rho), npairs, pc, pr, m, scale);
+    k_project<<<grid_for(npairs, 256, nsm), 256, 0, s>>>(reinterpret_cast<float4 *>(rho), npairs, pc, pr, m, scale,
+                                                         n, lower ? 1 : 0);
+}
+
+// Element (r, c) of rho; with lower (half storage) the upper triangle is taken from its mirror.
+__device__ __forceinline__ float2 pt_elem(const float2 *__restrict__ rho, uint64_t dim, uint64_t r, uint64_t c,
+                                          int lower)
+{
+    if (lower && r < c) {
+        const float2 v = rho[c * dim + r];
+        return make_float2(v.x, -v.y);
+    }
+    return rho[r * dim + c];
 }
 
 // Partial trace: out[a][a'] = sum_b rho[(a b), (a' b)] in FP64.
@@ -796,7 +812,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_ptrace_block(const float2 *__re
         for (uint64_t b = threadIdx.x; b < db; b += blockDim.x) {
             uint64_t off = 0;
             for (int j = 0; j < p.ntr; j++) off |= ((b >> (p.ntr - 1 - j)) & 1ull) << p.tpos[j];
-            float2 v = rho[(r0 | off) * dim + (c0 | off)];
+            const float2 v = pt_elem(rho, dim, r0 | off, c0 | off, p.lower);
             acc[0] += v.x;
             acc[1] += v.y;
         }
@@ -831,7 +847,7 @@ __global__ void k_ptrace_thread(const float2 *__restrict__ rho, PTParams p, doub
         for (uint64_t b = 0; b < db; b++) {
             uint64_t off = 0;
             for (int j = 0; j < p.ntr; j++) off |= ((b >> (p.ntr - 1 - j)) & 1ull) << p.tpos[j];
-            float2 v = rho[(r0 | off) * dim + (c0 | off)];
+            const float2 v = pt_elem(rho, dim, r0 | off, c0 | off, p.lower);
             sr += v.x;
             si += v.y;
         }

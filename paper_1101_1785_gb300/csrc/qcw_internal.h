@@ -61,6 +61,8 @@ struct GateKParams {   // one side (rows or columns) of a k-qubit dense gate, k 
 
 struct PTParams {
     int n, nkeep, ntr;
+    int lower;  // 1: only the lower triangle is current (half storage); (r, c) with r < c is read
+                // as conj(rho[c][r])
     int8_t kpos[QCW_MAX_QUBITS];  // label bit of kept qubit j; j = 0 is the result's MSB
     int8_t tpos[QCW_MAX_QUBITS];  // label bit of traced qubit j
 };
@@ -81,7 +83,7 @@ void launch_diag_reduce(const float2 *rho, int n, double *partials, double *out,
                         cudaStream_t s);
 void launch_purity(const float2 *rho, int n, double *partials, double *out, int nblocks,
                    cudaStream_t s);
-void launch_project(float2 *rho, int n, int qubit, int m, float scale, int nsm, cudaStream_t s);
+void launch_project(float2 *rho, int n, int qubit, int m, float scale, bool lower, int nsm, cudaStream_t s);
 // Half storage: rho[r][c] = conj(rho[c][r]) for r < c (complete the matrix from its lower
 // triangle), and purity from the lower triangle (2 |rho_rc|^2 below the diagonal).
 void launch_symmetrize(float2 *rho, int n, int nsm, cudaStream_t s);
