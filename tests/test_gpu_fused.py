@@ -333,8 +333,9 @@ def test_warp_specialised_wait_runs_out_and_context_recovers(q, kernel):
 def test_half_storage_readouts(q, n, kernel):
     """The warp-specialised pass leaves only the lower triangle current.  Readouts taken in that
     state (trace and probabilities from the diagonal, purity from the lower triangle, the
-    measurement's projection, the partial trace after the library completes the matrix) and the
-    completed state all match the oracle; a later pass on another kernel sees the full matrix."""
+    measurement's projection of the lower triangle, partial traces that read each upper element
+    as the conjugate of its mirror) and the completed state all match the oracle; a later pass
+    on another kernel sees the full matrix."""
     c = wl.random_circuit(n, 60, 9100 + n, "mixed", "adpd")
     want = oracle.run_circuit(c)
     d = q.Density(n)
@@ -349,8 +350,8 @@ def test_half_storage_readouts(q, n, kernel):
     m, p = d.measure(1, 0)
     assert m == m_ref and abs(p - p_ref) <= 1e-6
     assert abs(d.purity() - oracle.purity(want)) <= 1e-5
-    keep = [0, n - 1]
-    np.testing.assert_allclose(d.partial_trace(keep), oracle.partial_trace(want, keep), atol=1e-6, rtol=0)
+    for keep in ([0, n - 1], [1, n // 2, n - 2]):
+        np.testing.assert_allclose(d.partial_trace(keep), oracle.partial_trace(want, keep), atol=1e-6, rtol=0)
     # more work on the warp-specialised kernel, then on the per-tile Hermitian kernel
     tail = wl.random_circuit(n, 20, 9200 + n, "mixed", "adpd")
     for op in tail.ops:
