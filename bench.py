@@ -82,6 +82,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x: a job of independent replicas takes as long as its slowest
+    rank.  dist is torch.distributed (None: one process); device holds the reduction's tensor
+    (the GPU under NCCL, the CPU under gloo)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(gates_per_step: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job gate applications per second of `world` replicas, each running `steps` steps of
+    `gates_per_step` gates, over the slowest rank's time."""
+    return gates_per_step * steps * world / seconds
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -443,11 +462,7 @@ def run_ours(args):
     clocks = sampler.stop()
     d.enable_pass_timing(False)
     st = d.stats()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     tp, probs, meas, pt = out
     max_tr_err = max(abs(x[0] - 1) for x in tp)
 
@@ -470,20 +485,15 @@ def run_ours(args):
             ctxs[(k + 1) % 2].set_state_c64(host.data_ptr())
         gpu_step(ctxs[k % 2], packed, loaded=True)
     barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     d2.close()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
     accuracy = None
     if rank == 0 and not args.no_extras and nq == N_QUBITS:
         accuracy = accuracy_n14(d, packed)
     d.close()
 
-    total_gates = N_GATES * args.steps * world
-    value = total_gates / (ms / 1e3)
-    e2e_value = total_gates / e2e_s
+    value = replica_rate(N_GATES, args.steps, world, ms / 1e3)
+    e2e_value = replica_rate(N_GATES, args.steps, world, e2e_s)
 
     peaks, peak_kind = load_peaks()
     per_launch_bytes = pass_unit_bytes(nq)
