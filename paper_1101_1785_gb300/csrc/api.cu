@@ -553,11 +553,15 @@ extern "C" qcw_status qcw_reset(qcw_ctx *ctx)
 {
     CHECK_CTX(ctx);
     ctx->queue.clear();
-    ctx->half = false;
+    // In fused mode with the warp-specialised kernel (6 qubits and up) the next passes keep only
+    // the lower triangle current anyway: write that half of |0..0><0..0| and start in half storage.
+    ctx->half = ctx->mode == QCW_MODE_FUSED && ctx->n >= 6 &&
+                (ctx->fused_kernel == QCW_FUSED_KERNEL_AUTO || ctx->fused_kernel == QCW_FUSED_KERNEL_HERM_WS ||
+                 ctx->fused_kernel == QCW_FUSED_KERNEL_HERM_TC);
     ctx->state_ver++;
     qcw_status st = clear_error_word(ctx);
     if (st) return st;
-    launch_zero_state(ctx->rho, ctx->n, ctx->nsm, ctx->stream);
+    launch_zero_state(ctx->rho, ctx->n, ctx->half, ctx->nsm, ctx->stream);
     CKLAUNCH(ctx, 1);
     return QCW_OK;
 }

@@ -456,17 +456,23 @@ void launch_accumulate(float2 *acc, const float2 *x, int n, int nsm, cudaStream_
 }
 
 // --------------------------------------------------------------------- state set-up
-__global__ void k_zero_state(float4 *__restrict__ rho4, uint64_t n4)
+// |0..0><0..0|.  lower (half storage: only r >= c is current): element pairs wholly above the
+// diagonal are left alone (n is the register size).
+__global__ void k_zero_state(float4 *__restrict__ rho4, uint64_t n4, int n, int lower)
 {
+    const uint64_t cmask = (1ull << n) - 1;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n4;
-         t += (uint64_t)gridDim.x * blockDim.x)
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t g = 2 * t;
+        if (lower && (g & cmask) > (g >> n)) continue;
         rho4[t] = t == 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 }
 
-void launch_zero_state(float2 *rho, int n, int nsm, cudaStream_t s)
+void launch_zero_state(float2 *rho, int n, bool lower, int nsm, cudaStream_t s)
 {
     uint64_t n4 = (1ull << (2 * n)) / 2;
-    k_zero_state<<<grid_for(n4, 256, nsm), 256, 0, s>>>(reinterpret_cast<float4 *>(rho), n4);
+    k_zero_state<<<grid_for(n4, 256, nsm), 256, 0, s>>>(reinterpret_cast<float4 *>(rho), n4, n, lower ? 1 : 0);
 }
 
 __global__ void k_c128_to_c64(const double2 *__restrict__ src, float2 *__restrict__ dst, uint64_t cnt)

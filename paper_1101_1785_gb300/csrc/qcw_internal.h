@@ -74,7 +74,7 @@ void launch_super1(const Super1Params &p, float2 *rho, int n, int nsm, cudaStrea
 void launch_super2(const Super2Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_mono2(const Mono2Params &p, float2 *rho, int n, int nsm, cudaStream_t s);
 void launch_gatek_side(const GateKParams &p, float2 *rho, int n, int nsm, cudaStream_t s);
-void launch_zero_state(float2 *rho, int n, int nsm, cudaStream_t s);
+void launch_zero_state(float2 *rho, int n, bool lower, int nsm, cudaStream_t s);
 void launch_c128_to_c64(const double2 *src, float2 *dst, size_t count, int nsm, cudaStream_t s);
 void launch_c64_to_c128(const float2 *src, double2 *dst, size_t count, int nsm, cudaStream_t s);
 // Reductions write `nvals` doubles per block into partials, then fold them in block order.
